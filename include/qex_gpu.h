@@ -1,0 +1,205 @@
+/*
+ * qex_gpu.h -- C ABI of libqex_gpu.so: the even-odd staggered Dirac operator
+ * (with optional Naik term), its normal operator and conjugate-gradient
+ * solvers on one GB300 GPU (sm_103a).
+ *
+ * The paper (Jin & Osborn, "QEX: a framework for lattice field theories",
+ * Sec. 4) names the workload -- the staggered Dirac operator with the Naik
+ * term on SU(3) links, and single/double precision CG solvers for it
+ * (benchmarked with one right-hand side, Fig. 1) -- without printing a
+ * formula.  The operator implemented here is the standard one:
+ *
+ *   (D psi)(x) = sum_mu s_mu(x)   U_mu(x) psi(x+mu) - s_mu(x-mu)   U_mu(x-mu)^+ psi(x-mu)
+ *         + c3 sum_mu s3_mu(x)  W_mu(x) psi(x+3mu) - s3_mu(x-3mu) W_mu(x-3mu)^+ psi(x-3mu)
+ *
+ *   s_mu(y)  = eta_mu(y) * (-1 if mu = t, time is antiperiodic and y_t = Lt-1)
+ *   s3_mu(y) = eta_mu(y) * (-1 if mu = t, time is antiperiodic and y_t >= Lt-3)
+ *   eta_0 = 1, eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z)
+ *
+ * D flips site parity; D_eo (D_oe) is its block with even (odd) output.  The
+ * solvers invert the normal operator A = m^2 - D_eo D_oe on even sites.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Extents dims = {Lx, Ly, Lz, Lt}: all even and >= 2; >= 4 when the Naik
+ *   term is used.  V = Lx*Ly*Lz*Lt < 2^31, Vh = V/2.
+ * - Site lex = x + Lx*(y + Ly*(z + Lz*t)); parity = (x+y+z+t) mod 2; the
+ *   even-odd index of a site is parity*Vh + (lex >> 1).
+ * - Canonical ("lex") layouts, interleaved complex double, device memory:
+ *     links  [V][4][3][3]  (U_mu(x)_ab at ((lex*4 + mu)*3 + a)*3 + b)
+ *     fields [V][3]
+ * - Internal layouts (written by qex_pack_*; all other calls take these):
+ *     links: per parity p, per direction mu, structure-of-arrays planes over
+ *            the Vh sites of parity p.  F64: 9 planes of double2 (matrix
+ *            element c = 3a+b); F32: 4 planes of float4 (elements 0-1, 2-3,
+ *            4-5, 6-7) and 1 plane of float2 (element 8).  Size
+ *            qex_links_bytes().
+ *     half field (the Vh sites of one parity): F64: 3 planes of double2
+ *            (colour a); F32: 1 plane of float4 (colours 0,1) + 1 plane of
+ *            float2 (colour 2).  Size qex_field_bytes().
+ * - All field and link pointers are caller-owned DEVICE memory, 16-byte
+ *   aligned; the library never frees them.  The library owns only the
+ *   lattice object and its scratch (created lazily, freed by destroy).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous on it unless stated otherwise.
+ * - Every call checks its arguments before launching anything and returns a
+ *   qex_status; nothing aborts or traps.  qex_last_error() gives the message
+ *   of the calling thread's last failure.
+ * - A lattice object is not thread-safe: one host thread per lattice at a
+ *   time; its scratch is shared by all calls on it, so calls on one lattice
+ *   must be ordered on one stream.
+ */
+#ifndef QEX_GPU_H
+#define QEX_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QEX_OK = 0,
+    QEX_ERR_ARG = 1,             /* null pointer, bad parity/direction/hop, bad tolerance */
+    QEX_ERR_SHAPE = 2,           /* odd or too small extent, volume too large */
+    QEX_ERR_ALIGN = 3,           /* pointer not 16-byte aligned */
+    QEX_ERR_CUDA = 4,            /* a CUDA runtime call failed (message in qex_last_error) */
+    QEX_ERR_NOT_CONVERGED = 5,   /* solver hit maxiter; the result so far is returned */
+    QEX_ERR_TIMEOUT = 6,         /* reserved for bounded device-side waits */
+    QEX_ERR_NAN = 7              /* NaN/Inf met in a reduction, or CG breakdown */
+} qex_status;
+
+typedef enum { QEX_F64 = 0, QEX_F32 = 1 } qex_prec;
+
+typedef struct qex_lattice qex_lattice; /* opaque, owned by the library */
+
+typedef struct {
+    int iters;               /* operator applications inside the CG iteration   */
+    int reliable_updates;    /* FP64 true-residual recomputations (incl. final) */
+    int converged;           /* 1 if the FP64 true residual met tol             */
+    int reserved;
+    double true_rel_resid;   /* ||b - A x|| / ||b||, recomputed in FP64         */
+    double time_ms;          /* wall time of the solve on the stream            */
+} qex_cg_stats;
+
+/* ---------------------------------------------------------------- lattice */
+
+/* Create a lattice of extents dims[4] = {Lx,Ly,Lz,Lt}; antiperiodic_t != 0
+ * makes time antiperiodic for fermions.  Errors: QEX_ERR_ARG (null),
+ * QEX_ERR_SHAPE (odd extent, extent < 2, V >= 2^31). */
+qex_status qex_lattice_create(const int dims[4], int antiperiodic_t, qex_lattice **out);
+
+/* Free the lattice and all scratch it owns (synchronises the device first).
+ * NULL is accepted. */
+qex_status qex_lattice_destroy(qex_lattice *lat);
+
+/* Volume V and half volume Vh. */
+int64_t qex_volume(const qex_lattice *lat);
+int64_t qex_half_volume(const qex_lattice *lat);
+
+/* Even-odd index parity*Vh + (lex >> 1) of coord[4] = {x,y,z,t}
+ * (host function; -1 on bad arguments). */
+int64_t qex_eo_index(const qex_lattice *lat, const int coord[4]);
+
+/* Neighbour table: for the i-th site x of parity `parity` (i in [0,Vh)),
+ * host_out[i] = index, within the opposite parity, of x + hop*mu_hat
+ * (periodic wrap), hop in {+1,-1,+3,-3}.  Computed on the host with the same
+ * index arithmetic the kernels use.  host_out holds Vh int32. */
+qex_status qex_neighbor_table(const qex_lattice *lat, int parity, int mu, int hop, int32_t *host_out);
+
+/* Same table written by a kernel into device memory dev_out (Vh int32). */
+qex_status qex_neighbor_table_device(const qex_lattice *lat, int parity, int mu, int hop,
+                                     int32_t *dev_out, void *stream);
+
+/* ---------------------------------------------------------------- layout */
+
+/* Bytes of one internal link set (4V links) and of one internal half field. */
+size_t qex_links_bytes(const qex_lattice *lat, qex_prec prec);
+size_t qex_field_bytes(const qex_lattice *lat, qex_prec prec);
+
+/* Canonical lex links (complex double, [V][4][3][3]) -> internal links of
+ * precision prec (F32 rounds to nearest).  lex_links and internal must not
+ * overlap. */
+qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *lex_links,
+                          void *internal, void *stream);
+
+/* Internal links -> canonical lex links (complex double). */
+qex_status qex_unpack_links(const qex_lattice *lat, qex_prec prec, const void *internal,
+                            double *lex_links, void *stream);
+
+/* Sites of parity `parity` of a canonical full-lattice field ([V][3] complex
+ * double) -> internal half field of precision prec. */
+qex_status qex_pack_field(const qex_lattice *lat, qex_prec prec, int parity, const double *lex_field,
+                          void *half, void *stream);
+
+/* Internal half field -> the parity-`parity` sites of a canonical field
+ * (sites of the other parity are left untouched). */
+qex_status qex_unpack_field(const qex_lattice *lat, qex_prec prec, int parity, const void *half,
+                            double *lex_field, void *stream);
+
+/* Precision conversion of internal links or half fields (F64 -> F32 rounds
+ * to nearest, F32 -> F64 is exact).  in and out must not overlap. */
+qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to,
+                             void *out, void *stream);
+qex_status qex_convert_field(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to,
+                             void *out, void *stream);
+
+/* ---------------------------------------------------------------- operator */
+
+/* out = D_{p,1-p} in (p = out_parity): the staggered operator from the
+ * parity-(1-p) half field `in` to the parity-p half field `out`.  fat: one
+ * internal link set (U); lng: long links W for the Naik term, or NULL;
+ * c_naik: the Naik coefficient c3 (ignored when lng is NULL).  in, out, fat,
+ * lng share precision prec.  in and out must not overlap. */
+qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
+                      double c_naik, int out_parity, const void *in, void *out, void *stream);
+
+/* out = (m^2 - D_eo D_oe) in on even sites; tmp_odd is a caller half field
+ * (odd sites) that receives D_oe in. */
+qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
+                         double c_naik, double mass, const void *in, void *out, void *tmp_odd,
+                         void *stream);
+
+/* ||f||^2 of a half field, accumulated in FP64 in a fixed order
+ * (bit-reproducible run to run); written to dev_out (one double, device). */
+qex_status qex_norm2(const qex_lattice *lat, qex_prec prec, const void *f, double *dev_out,
+                     void *stream);
+
+/* <a, b> = sum conj(a) b over a half field, FP64 accumulation, fixed order;
+ * dev_out receives {re, im} (two doubles, device). */
+qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const void *b,
+                   double *dev_out, void *stream);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* Solve (m^2 - D_eo D_oe) x = b on even sites to a true relative residual
+ * ||b - A x|| / ||b|| <= tol, computed in FP64.
+ *
+ * inner = QEX_F64: plain CG in FP64 on fat64/lng64.
+ * inner = QEX_F32: mixed precision: the CG iteration runs in FP32 on
+ *   fat32/lng32 (inner residual and iterate in FP32, all reductions in FP64);
+ *   whenever the iterated residual norm drops below delta times its maximum
+ *   since the last update (or meets tol), the FP64 solution is updated and the
+ *   residual is recomputed in FP64 with fat64/lng64 (reliable update).
+ * b64, x64: F64 even half fields; x64 holds the initial guess on entry and the
+ *   solution on return.  lng64/lng32 NULL = no Naik term.
+ * Synchronises the stream before returning (fills stats, may be NULL).
+ * Returns QEX_ERR_NOT_CONVERGED after maxiter iterations (x64 holds the last
+ * iterate), QEX_ERR_NAN on a NaN/Inf or a non-positive <p, A p>. */
+qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
+                  const void *fat32, const void *lng32, double c_naik, double mass, const void *b64,
+                  void *x64, double tol, int maxiter, double delta, void *stream,
+                  qex_cg_stats *stats);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *qex_last_error(void);
+
+/* Library version string. */
+const char *qex_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QEX_GPU_H */

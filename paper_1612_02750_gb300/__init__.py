@@ -1,0 +1,325 @@
+"""GB300 even-odd staggered Dirac operator and CG solvers (libqex_gpu).
+
+Thin Python binding of the C ABI declared in ``include/qex_gpu.h``: every
+function here has the name of the C entry point it calls and only marshals
+arguments (torch tensors -> device pointers, the current torch CUDA stream ->
+``cudaStream_t``, status codes -> exceptions).  All arithmetic runs in the
+library's CUDA kernels; there is no CPU fallback -- importing works without a
+GPU, but any call that needs the library raises if ``libqex_gpu.so`` is not
+built or no CUDA device is present.
+
+Tensors: canonical links are complex128 ``[Lt, Lz, Ly, Lx, 4, 3, 3]`` and
+canonical fields complex128 ``[Lt, Lz, Ly, Lx, 3]`` (``fieldgen`` layout);
+internal link sets and half fields are flat float64 (F64) or float32 (F32)
+tensors of ``qex_links_bytes`` / ``qex_field_bytes`` bytes.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+F64 = 0
+F32 = 1
+_PREC = {"f64": F64, "f32": F32, F64: F64, F32: F32, torch.float64: F64, torch.float32: F32}
+_DTYPE = {F64: torch.float64, F32: torch.float32}
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_ALIGN", 4: "ERR_CUDA",
+           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_NAN"}
+
+_lib = None
+
+
+class QexError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libqex_gpu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libqex_gpu.so is not built ({_build.LIB}); run paper_1612_02750_gb300.build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i, d, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_size_t
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "qex_lattice_create": (i, [ip, i, ctypes.POINTER(vp)]),
+        "qex_lattice_destroy": (i, [vp]),
+        "qex_volume": (i64, [vp]),
+        "qex_half_volume": (i64, [vp]),
+        "qex_eo_index": (i64, [vp, ip]),
+        "qex_neighbor_table": (i, [vp, i, i, i, vp]),
+        "qex_neighbor_table_device": (i, [vp, i, i, i, vp, vp]),
+        "qex_links_bytes": (sz, [vp, i]),
+        "qex_field_bytes": (sz, [vp, i]),
+        "qex_pack_links": (i, [vp, i, vp, vp, vp]),
+        "qex_unpack_links": (i, [vp, i, vp, vp, vp]),
+        "qex_pack_field": (i, [vp, i, i, vp, vp, vp]),
+        "qex_unpack_field": (i, [vp, i, i, vp, vp, vp]),
+        "qex_convert_links": (i, [vp, i, vp, i, vp, vp]),
+        "qex_convert_field": (i, [vp, i, vp, i, vp, vp]),
+        "qex_dslash": (i, [vp, i, vp, vp, d, i, vp, vp, vp]),
+        "qex_normal_op": (i, [vp, i, vp, vp, d, d, vp, vp, vp, vp]),
+        "qex_norm2": (i, [vp, i, vp, vp, vp]),
+        "qex_dot": (i, [vp, i, vp, vp, vp, vp]),
+        "qex_cg": (i, [vp, i, vp, vp, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_last_error": (ctypes.c_char_p, []),
+        "qex_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding wraps."""
+    return ["qex_lattice_create", "qex_lattice_destroy", "qex_volume", "qex_half_volume", "qex_eo_index",
+            "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
+            "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
+            "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
+            "qex_last_error", "qex_version"]
+
+
+def _check(status: int):
+    if status != 0:
+        raise QexError(status, load().qex_last_error().decode())
+
+
+def _prec(p) -> int:
+    try:
+        return _PREC[p]
+    except KeyError:
+        raise ValueError(f"unknown precision {p!r}") from None
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Lattice:
+    """Owning handle of a ``qex_lattice`` (extents ``dims = (Lx, Ly, Lz, Lt)``)."""
+
+    def __init__(self, dims, antiperiodic: bool = True):
+        lib = load()
+        self.dims = tuple(int(v) for v in dims)
+        self.antiperiodic = bool(antiperiodic)
+        h = ctypes.c_void_p()
+        _check(lib.qex_lattice_create((ctypes.c_int * 4)(*self.dims), int(antiperiodic), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def volume(self) -> int:
+        return int(load().qex_volume(self._h))
+
+    @property
+    def half_volume(self) -> int:
+        return int(load().qex_half_volume(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load().qex_lattice_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ----------------------------------------------------------------- geometry
+
+def qex_lattice_create(dims, antiperiodic: bool = True) -> Lattice:
+    return Lattice(dims, antiperiodic)
+
+
+def qex_lattice_destroy(lat: Lattice) -> None:
+    lat.close()
+
+
+def qex_eo_index(lat: Lattice, coord) -> int:
+    return int(load().qex_eo_index(lat.handle, (ctypes.c_int * 4)(*coord)))
+
+
+def qex_neighbor_table(lat: Lattice, parity: int, mu: int, hop: int):
+    import numpy as np
+
+    out = np.empty(lat.half_volume, dtype=np.int32)
+    _check(load().qex_neighbor_table(lat.handle, parity, mu, hop, out.ctypes.data))
+    return out
+
+
+def qex_neighbor_table_device(lat: Lattice, parity: int, mu: int, hop: int, out=None, stream=None):
+    if out is None:
+        out = torch.empty(lat.half_volume, dtype=torch.int32, device="cuda")
+    _check(load().qex_neighbor_table_device(lat.handle, parity, mu, hop, _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_links_bytes(lat: Lattice, prec) -> int:
+    return int(load().qex_links_bytes(lat.handle, _prec(prec)))
+
+
+def qex_field_bytes(lat: Lattice, prec) -> int:
+    return int(load().qex_field_bytes(lat.handle, _prec(prec)))
+
+
+def empty_links(lat: Lattice, prec, device="cuda"):
+    p = _prec(prec)
+    return torch.empty(qex_links_bytes(lat, p) // _DTYPE[p].itemsize, dtype=_DTYPE[p], device=device)
+
+
+def empty_field(lat: Lattice, prec, device="cuda"):
+    p = _prec(prec)
+    return torch.empty(qex_field_bytes(lat, p) // _DTYPE[p].itemsize, dtype=_DTYPE[p], device=device)
+
+
+def zeros_field(lat: Lattice, prec, device="cuda"):
+    return empty_field(lat, prec, device).zero_()
+
+
+# ------------------------------------------------------------------- layout
+
+def qex_pack_links(lat: Lattice, prec, lex_links, out=None, stream=None):
+    if lex_links.dtype != torch.complex128:
+        raise TypeError("canonical links must be complex128")
+    out = empty_links(lat, prec) if out is None else out
+    _check(load().qex_pack_links(lat.handle, _prec(prec), _ptr(lex_links), _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_unpack_links(lat: Lattice, prec, internal, out=None, stream=None):
+    if out is None:
+        lx, ly, lz, lt = lat.dims
+        out = torch.empty((lt, lz, ly, lx, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    _check(load().qex_unpack_links(lat.handle, _prec(prec), _ptr(internal), _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_pack_field(lat: Lattice, prec, parity: int, lex_field, out=None, stream=None):
+    if lex_field.dtype != torch.complex128:
+        raise TypeError("canonical fields must be complex128")
+    out = empty_field(lat, prec) if out is None else out
+    _check(load().qex_pack_field(lat.handle, _prec(prec), parity, _ptr(lex_field), _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_unpack_field(lat: Lattice, prec, parity: int, half, out=None, stream=None):
+    if out is None:
+        lx, ly, lz, lt = lat.dims
+        out = torch.zeros((lt, lz, ly, lx, 3), dtype=torch.complex128, device="cuda")
+    _check(load().qex_unpack_field(lat.handle, _prec(prec), parity, _ptr(half), _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_convert_links(lat: Lattice, src_prec, internal, dst_prec, out=None, stream=None):
+    out = empty_links(lat, dst_prec) if out is None else out
+    _check(load().qex_convert_links(lat.handle, _prec(src_prec), _ptr(internal), _prec(dst_prec), _ptr(out),
+                                    _stream(stream)))
+    return out
+
+
+def qex_convert_field(lat: Lattice, src_prec, half, dst_prec, out=None, stream=None):
+    out = empty_field(lat, dst_prec) if out is None else out
+    _check(load().qex_convert_field(lat.handle, _prec(src_prec), _ptr(half), _prec(dst_prec), _ptr(out),
+                                    _stream(stream)))
+    return out
+
+
+# ----------------------------------------------------------------- operator
+
+def qex_dslash(lat: Lattice, prec, fat, lng, c_naik: float, out_parity: int, inp, out=None, stream=None):
+    out = empty_field(lat, prec) if out is None else out
+    _check(load().qex_dslash(lat.handle, _prec(prec), _ptr(fat), _ptr(lng), float(c_naik), int(out_parity),
+                             _ptr(inp), _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_normal_op(lat: Lattice, prec, fat, lng, c_naik: float, mass: float, inp, out=None, tmp_odd=None,
+                  stream=None):
+    out = empty_field(lat, prec) if out is None else out
+    tmp_odd = empty_field(lat, prec) if tmp_odd is None else tmp_odd
+    _check(load().qex_normal_op(lat.handle, _prec(prec), _ptr(fat), _ptr(lng), float(c_naik), float(mass),
+                                _ptr(inp), _ptr(out), _ptr(tmp_odd), _stream(stream)))
+    return out
+
+
+def qex_norm2(lat: Lattice, prec, f, out=None, stream=None):
+    out = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+    _check(load().qex_norm2(lat.handle, _prec(prec), _ptr(f), _ptr(out), _stream(stream)))
+    return out
+
+
+def qex_dot(lat: Lattice, prec, a, b, out=None, stream=None):
+    out = torch.empty(2, dtype=torch.float64, device="cuda") if out is None else out
+    _check(load().qex_dot(lat.handle, _prec(prec), _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------ solvers
+
+def qex_cg(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, mass: float, b64, x64,
+           tol: float = 1e-10, maxiter: int = 100000, delta: float = 0.1, stream=None, check: bool = True):
+    """Solve (m^2 - D_eo D_oe) x = b; x64 is the initial guess, overwritten.
+    Returns (status, stats dict); raises on error when ``check``."""
+    stats = CgStats()
+    st = load().qex_cg(lat.handle, _prec(inner), _ptr(fat64), _ptr(lng64), _ptr(fat32), _ptr(lng32),
+                       float(c_naik), float(mass), _ptr(b64), _ptr(x64), float(tol), int(maxiter), float(delta),
+                       _stream(stream), ctypes.byref(stats))
+    if check:
+        _check(st)
+    return st, stats.as_dict()
+
+
+def qex_last_error() -> str:
+    return load().qex_last_error().decode()
+
+
+def qex_version() -> str:
+    return load().qex_version().decode()

@@ -1,0 +1,304 @@
+// blas.cu -- fused CG vector updates and deterministic FP64 reductions.
+//
+// Grid-stride kernels over the Vh sites of one parity with a fixed grid per
+// lattice (at most 8 blocks per SM), so the per-block partial sums -- and
+// therefore every reduction -- come out bit-identical run to run.  Sums are
+// formed per site in the vector precision and accumulated across sites in
+// FP64.
+#include "qex_kernels.cuh"
+
+namespace qex {
+
+// Block partial -> partials[]; the last block sums them in index order.
+// Returns true in thread 0 of the last block, with *tot set.
+__device__ __forceinline__ bool grid_sum(double part, double *partials, unsigned int *counter, double *smem,
+                                         double *tot) {
+    __shared__ unsigned int is_last;
+    const double bs = block_sum(part, smem);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = bs;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    const double s = block_sum_partials(partials, gridDim.x, smem);
+    if (threadIdx.x != 0) return false;
+    *counter = 0u;
+    *tot = s;
+    return true;
+}
+
+template <typename R>
+__device__ __forceinline__ R norm2_site(const Vec3<R> &v) {
+    R s = v.c[0].re * v.c[0].re;
+    s = fma(v.c[0].im, v.c[0].im, s);
+#pragma unroll
+    for (int a = 1; a < 3; ++a) {
+        s = fma(v.c[a].re, v.c[a].re, s);
+        s = fma(v.c[a].im, v.c[a].im, s);
+    }
+    return s;
+}
+
+// x += alpha p; r -= alpha ap; ||r||^2 -> rr_new; then the CG scalar logic.
+template <typename R>
+__global__ void __launch_bounds__(kBlock)
+update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, const R *__restrict__ p,
+                 const R *__restrict__ ap, CgScalars *S, double *partials, unsigned int *counter) {
+    __shared__ double smem[32];
+    if (S->halt) return;
+    const R alpha = (R)S->alpha;
+    double part = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+        Vec3<R> xv = load_vec(x, vh, i), rv = load_vec(r, vh, i);
+        const Vec3<R> pv = load_vec(p, vh, i), av = load_vec(ap, vh, i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
+            xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
+            rv.c[a].re = fma(-alpha, av.c[a].re, rv.c[a].re);
+            rv.c[a].im = fma(-alpha, av.c[a].im, rv.c[a].im);
+        }
+        store_vec(x, vh, i, xv);
+        store_vec(r, vh, i, rv);
+        part += (double)norm2_site(rv);
+    }
+    double rr_new;
+    if (!grid_sum(part, partials, counter, smem, &rr_new)) return;
+    S->iters += 1;
+    if (!isfinite(rr_new)) {
+        S->error = 1;
+        S->halt = 1;
+        return;
+    }
+    if (rr_new > S->rmax2) S->rmax2 = rr_new;
+    if (rr_new <= S->stop2 || rr_new < S->delta2 * S->rmax2 || S->iters >= S->maxiter) {
+        // FP64 true residual next (reliable update / convergence check); rr
+        // keeps the previous value so that beta is formed from the true one
+        S->need_ru = 1;
+        S->halt = 1;
+        return;
+    }
+    S->beta = rr_new / S->rr;
+    S->rr = rr_new;
+}
+
+// p = r + beta p
+template <typename R>
+__global__ void __launch_bounds__(kBlock)
+update_p_kernel(int vh, const R *__restrict__ r, R *__restrict__ p, CgScalars *S, int check_halt) {
+    if (check_halt && S->halt) return;
+    const R beta = (R)S->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+        const Vec3<R> rv = load_vec(r, vh, i);
+        Vec3<R> pv = load_vec(p, vh, i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            pv.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+            pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+        }
+        store_vec(p, vh, i, pv);
+    }
+}
+
+// x64 += xh32; xh32 = 0
+__global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restrict__ x, float *__restrict__ xh) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+        Vec3<double> xv = load_vec(x, vh, i);
+        const Vec3<float> hv = load_vec(xh, vh, i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xv.c[a].re += (double)hv.c[a].re;
+            xv.c[a].im += (double)hv.c[a].im;
+        }
+        store_vec(x, vh, i, xv);
+        Vec3<float> z;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) z.c[a].re = z.c[a].im = 0.f;
+        store_vec(xh, vh, i, z);
+    }
+}
+
+// r32 = (float) r64; p32 = r32 + beta p32
+__global__ void __launch_bounds__(kBlock)
+lower_r_update_p_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ p32,
+                        const CgScalars *S) {
+    const float beta = (float)S->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+        const Vec3<double> rd = load_vec(r64, vh, i);
+        Vec3<float> rv, pv = load_vec(p32, vh, i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            rv.c[a].re = (float)rd.c[a].re;
+            rv.c[a].im = (float)rd.c[a].im;
+            pv.c[a].re = fmaf(beta, pv.c[a].re, rv.c[a].re);
+            pv.c[a].im = fmaf(beta, pv.c[a].im, rv.c[a].im);
+        }
+        store_vec(r32, vh, i, rv);
+        store_vec(p32, vh, i, pv);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock)
+norm2_kernel(int vh, const R *__restrict__ f, double *out, CgScalars *S, double *partials, unsigned int *counter) {
+    __shared__ double smem[32];
+    double part = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x)
+        part += (double)norm2_site(load_vec(f, vh, i));
+    double tot;
+    if (!grid_sum(part, partials, counter, smem, &tot)) return;
+    if (out) *out = tot;
+    if (S) {
+        S->bb = tot;
+        S->stop2 = S->tol2 * tot;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock)
+dot_kernel(int vh, const R *__restrict__ a, const R *__restrict__ b, double *out, double *partials,
+           unsigned int *counter) {
+    __shared__ double smem[32];
+    __shared__ double re_tot;
+    double pre = 0.0, pim = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+        const Vec3<R> av = load_vec(a, vh, i), bv = load_vec(b, vh, i);
+        R re = R(0), im = R(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {  // conj(a) b
+            re = fma(av.c[c].re, bv.c[c].re, re);
+            re = fma(av.c[c].im, bv.c[c].im, re);
+            im = fma(av.c[c].re, bv.c[c].im, im);
+            im = fma(-av.c[c].im, bv.c[c].re, im);
+        }
+        pre += (double)re;
+        pim += (double)im;
+    }
+    // two fixed-order grid sums over disjoint halves of the partials buffer
+    double t0;
+    unsigned int nb = gridDim.x;
+    const double bre = block_sum(pre, smem);
+    const double bim = block_sum(pim, smem);
+    __shared__ unsigned int is_last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = bre;
+        partials[nb + blockIdx.x] = bim;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == nb - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    t0 = block_sum_partials(partials, nb, smem);
+    if (threadIdx.x == 0) re_tot = t0;
+    const double t1 = block_sum_partials(partials + nb, nb, smem);
+    if (threadIdx.x != 0) return;
+    *counter = 0u;
+    out[0] = re_tot;
+    out[1] = t1;
+}
+
+qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, const void *p, const void *ap,
+                            CgScalars *S, cudaStream_t st) {
+    int nb = blas_blocks(lat), vh = (int)lat->vh;
+    if (prec == QEX_F64)
+        update_xr_kernel<double><<<nb, kBlock, 0, st>>>(vh, (double *)x, (double *)r, (const double *)p,
+                                                        (const double *)ap, S, lat->partials, lat->counter);
+    else
+        update_xr_kernel<float><<<nb, kBlock, 0, st>>>(vh, (float *)x, (float *)r, (const float *)p,
+                                                       (const float *)ap, S, lat->partials, lat->counter);
+    QEX_CHECK_LAUNCH("update_xr_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *p, CgScalars *S, int check_halt,
+                           cudaStream_t st) {
+    int nb = blas_blocks(lat), vh = (int)lat->vh;
+    if (prec == QEX_F64)
+        update_p_kernel<double><<<nb, kBlock, 0, st>>>(vh, (const double *)r, (double *)p, S, check_halt);
+    else
+        update_p_kernel<float><<<nb, kBlock, 0, st>>>(vh, (const float *)r, (float *)p, S, check_halt);
+    QEX_CHECK_LAUNCH("update_p_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st) {
+    accum_x_kernel<<<blas_blocks(lat), kBlock, 0, st>>>((int)lat->vh, x64, xh32);
+    QEX_CHECK_LAUNCH("accum_x_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_lower_r_update_p(qex_lattice *lat, const double *r64, float *r32, float *p32, CgScalars *S,
+                                   cudaStream_t st) {
+    lower_r_update_p_kernel<<<blas_blocks(lat), kBlock, 0, st>>>((int)lat->vh, r64, r32, p32, S);
+    QEX_CHECK_LAUNCH("lower_r_update_p_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_norm2(qex_lattice *lat, qex_prec prec, const void *f, double *out, CgScalars *S, cudaStream_t st) {
+    qex_status s = ensure_scratch(lat);
+    if (s) return s;
+    int nb = blas_blocks(lat), vh = (int)lat->vh;
+    if (prec == QEX_F64)
+        norm2_kernel<double><<<nb, kBlock, 0, st>>>(vh, (const double *)f, out, S, lat->partials, lat->counter);
+    else
+        norm2_kernel<float><<<nb, kBlock, 0, st>>>(vh, (const float *)f, out, S, lat->partials, lat->counter);
+    QEX_CHECK_LAUNCH("norm2_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_dot(qex_lattice *lat, qex_prec prec, const void *a, const void *b, double *out, cudaStream_t st) {
+    qex_status s = ensure_scratch(lat);
+    if (s) return s;
+    int nb = blas_blocks(lat), vh = (int)lat->vh;
+    if (prec == QEX_F64)
+        dot_kernel<double><<<nb, kBlock, 0, st>>>(vh, (const double *)a, (const double *)b, out, lat->partials,
+                                                  lat->counter);
+    else
+        dot_kernel<float><<<nb, kBlock, 0, st>>>(vh, (const float *)a, (const float *)b, out, lat->partials,
+                                                 lat->counter);
+    QEX_CHECK_LAUNCH("dot_kernel");
+    return QEX_OK;
+}
+
+}  // namespace qex
+
+using namespace qex;
+
+extern "C" {
+
+qex_status qex_norm2(const qex_lattice *lat, qex_prec prec, const void *f, double *dev_out, void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec))) return st;
+    if (!f || !dev_out) {
+        set_error("field and dev_out must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    if (!aligned16(f)) {
+        set_error("field must be 16-byte aligned");
+        return QEX_ERR_ALIGN;
+    }
+    return launch_norm2(const_cast<qex_lattice *>(lat), prec, f, dev_out, nullptr, as_stream(stream));
+}
+
+qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const void *b, double *dev_out,
+                   void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec))) return st;
+    if (!a || !b || !dev_out) {
+        set_error("fields and dev_out must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    if (!aligned16(a) || !aligned16(b)) {
+        set_error("fields must be 16-byte aligned");
+        return QEX_ERR_ALIGN;
+    }
+    return launch_dot(const_cast<qex_lattice *>(lat), prec, a, b, dev_out, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// dslash.cu -- the even-odd staggered operator D_{p,1-p} (one-hop term plus
+// optional Naik three-hop term) and its CG epilogues.
+//
+// One thread per output site of parity p.  Per site the kernel reads the
+// four forward links stored at the site, the four backward links stored at
+// the neighbours x - mu (block 1-p of the link set), and the eight neighbour
+// colour vectors of the input half field; with the Naik term the same again
+// for the long links and the x +- 3mu neighbours.  Staggered phases and the
+// antiperiodic time boundary are computed from the site coordinates; no phase
+// is folded into the links.
+#include "qex_kernels.cuh"
+
+namespace qex {
+
+template <typename R, bool NAIK, int EPI>
+__global__ void __launch_bounds__(kBlock)
+dslash_kernel(Geom g, const R *__restrict__ fat, const R *__restrict__ lng, R c3, int p,
+              const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ q,
+              const double *__restrict__ b, R m2, CgScalars *S, int check_halt,
+              double *partials, unsigned int *counter) {
+    __shared__ double smem[32];
+    __shared__ unsigned int is_last;
+    if (check_halt && S->halt) return;  // uniform over the grid
+
+    const size_t vh = (size_t)g.vh;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (i < g.vh) {
+        const Site s = site_of(g, p, i);
+        Vec3<R> acc;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = R(0);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const R eta = eta_bit(s, mu) ? R(-1) : R(1);
+            {   // + eta b U_mu(x) psi(x + mu)
+                const int j = hop_index(g, s, mu, 1);
+                const Mat3<R> u = load_link(fat, vh, p, mu, i);
+                const Vec3<R> v = load_vec(in, vh, j);
+                acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, v);
+            }
+            {   // - eta b U_mu(x - mu)^+ psi(x - mu)
+                const int j = hop_index(g, s, mu, -1);
+                const Mat3<R> u = load_link(fat, vh, 1 - p, mu, j);
+                const Vec3<R> v = load_vec(in, vh, j);
+                acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, v);
+            }
+            if (NAIK) {
+                const R e3 = c3 * eta;
+                {
+                    const int j = hop_index(g, s, mu, 3);
+                    const Mat3<R> u = load_link(lng, vh, p, mu, i);
+                    const Vec3<R> v = load_vec(in, vh, j);
+                    acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, v);
+                }
+                {
+                    const int j = hop_index(g, s, mu, -3);
+                    const Mat3<R> u = load_link(lng, vh, 1 - p, mu, j);
+                    const Vec3<R> v = load_vec(in, vh, j);
+                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, v);
+                }
+            }
+        }
+        if (EPI == EPI_PLAIN) {
+            store_vec(out, vh, i, acc);
+        } else if (EPI == EPI_NORMAL) {
+            // out = m^2 q - D in;  part = Re <q, out>
+            const Vec3<R> qv = load_vec(q, vh, i);
+            Vec3<R> o;
+            R d = R(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = fma(m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = fma(m2, qv.c[a].im, -acc.c[a].im);
+                d = fma(qv.c[a].re, o.c[a].re, d);
+                d = fma(qv.c[a].im, o.c[a].im, d);
+            }
+            store_vec(out, vh, i, o);
+            part = (double)d;
+        } else {
+            // out = b - m^2 q + D in;  part = ||out||^2   (FP64 only)
+            const Vec3<R> qv = load_vec(q, vh, i);
+            const Vec3<double> bv = load_vec(b, vh, i);
+            Vec3<R> o;
+            double d = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = (R)bv.c[a].re - fma(m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = (R)bv.c[a].im - fma(m2, qv.c[a].im, -acc.c[a].im);
+                d = fma((double)o.c[a].re, (double)o.c[a].re, d);
+                d = fma((double)o.c[a].im, (double)o.c[a].im, d);
+            }
+            store_vec(out, vh, i, o);
+            part = d;
+        }
+    }
+    if (EPI == EPI_PLAIN || S == nullptr) return;  // S is uniform over the grid
+
+    // Deterministic grid reduction: block sums -> partials; the last block to
+    // finish sums the partials in index order and updates the CG scalars.
+    const double bs = block_sum(part, smem);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = bs;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const double tot = block_sum_partials(partials, gridDim.x, smem);
+    if (threadIdx.x != 0) return;
+    *counter = 0u;
+    if (EPI == EPI_NORMAL) {
+        S->pAp = tot;
+        if (!(tot > 0.0) || !isfinite(tot)) {
+            S->error = isfinite(tot) ? 2 : 1;
+            S->halt = 1;
+        } else {
+            S->alpha = S->rr / tot;
+        }
+    } else {
+        // FP64 true residual: accept convergence or continue with beta from it
+        S->true_rr = tot;
+        S->reliable_updates += 1;
+        if (!isfinite(tot)) {
+            S->error = 1;
+            S->halt = 1;
+            return;
+        }
+        S->beta = S->rr > 0.0 ? tot / S->rr : 0.0;
+        S->rr = tot;
+        S->rmax2 = tot;
+        S->need_ru = 0;
+        S->done = tot <= S->stop2 ? 1 : 0;
+        S->halt = (S->done || S->iters >= S->maxiter) ? 1 : 0;
+    }
+}
+
+template <typename R, bool NAIK, int EPI>
+static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
+    int nb = blocks_for(lat->vh);
+    dslash_kernel<R, NAIK, EPI><<<nb, kBlock, 0, st>>>(
+        lat->geom, (const R *)a.fat, (const R *)a.lng, (R)a.c3, a.out_parity, (const R *)a.in, (R *)a.out,
+        (const R *)a.q, a.b, (R)a.m2, a.S, a.check_halt, lat->partials, lat->counter);
+}
+
+template <typename R, bool NAIK>
+static void launch_epi(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
+    if (a.epi == EPI_PLAIN)
+        launch_t<R, NAIK, EPI_PLAIN>(lat, a, st);
+    else if (a.epi == EPI_NORMAL)
+        launch_t<R, NAIK, EPI_NORMAL>(lat, a, st);
+    else
+        launch_t<R, NAIK, EPI_RESID>(lat, a, st);
+}
+
+qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
+    if (a.S) {
+        qex_status s = ensure_scratch(lat);
+        if (s) return s;
+    }
+    if (a.prec == QEX_F64) {
+        if (a.lng)
+            launch_epi<double, true>(lat, a, st);
+        else
+            launch_epi<double, false>(lat, a, st);
+    } else {
+        if (a.epi == EPI_RESID) {
+            set_error("the residual epilogue is FP64 only");
+            return QEX_ERR_ARG;
+        }
+        if (a.lng)
+            launch_epi<float, true>(lat, a, st);
+        else
+            launch_epi<float, false>(lat, a, st);
+    }
+    QEX_CHECK_LAUNCH("dslash_kernel");
+    return QEX_OK;
+}
+
+qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
+                             const void *in, const void *out) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec))) return st;
+    if (!fat || !in || !out) {
+        set_error("fat, in and out must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    if (!aligned16(fat) || !aligned16(in) || !aligned16(out) || (lng && !aligned16(lng))) {
+        set_error("links and fields must be 16-byte aligned");
+        return QEX_ERR_ALIGN;
+    }
+    if (in == out) {
+        set_error("in and out must not alias");
+        return QEX_ERR_ARG;
+    }
+    if (lng) {
+        for (int mu = 0; mu < 4; ++mu)
+            if (lat->dims[mu] < 4) {
+                set_error("the Naik term needs every extent >= 4");
+                return QEX_ERR_SHAPE;
+            }
+    }
+    return QEX_OK;
+}
+
+}  // namespace qex
+
+using namespace qex;
+
+extern "C" {
+
+qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, double c_naik,
+                      int out_parity, const void *in, void *out, void *stream) {
+    qex_status st = check_dslash_args(lat, prec, fat, lng, in, out);
+    if (st) return st;
+    if (out_parity != 0 && out_parity != 1) {
+        set_error("out_parity must be 0 or 1");
+        return QEX_ERR_ARG;
+    }
+    DslashArgs a = {};
+    a.prec = prec;
+    a.fat = fat;
+    a.lng = lng;
+    a.c3 = c_naik;
+    a.out_parity = out_parity;
+    a.in = in;
+    a.out = out;
+    a.epi = EPI_PLAIN;
+    return launch_dslash(const_cast<qex_lattice *>(lat), a, as_stream(stream));
+}
+
+qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, double c_naik,
+                         double mass, const void *in, void *out, void *tmp_odd, void *stream) {
+    qex_status st = check_dslash_args(lat, prec, fat, lng, in, out);
+    if (st) return st;
+    if (!tmp_odd || !aligned16(tmp_odd) || tmp_odd == in || tmp_odd == out) {
+        set_error("tmp_odd must be a separate, 16-byte aligned half field");
+        return QEX_ERR_ARG;
+    }
+    qex_lattice *l = const_cast<qex_lattice *>(lat);
+    cudaStream_t s = as_stream(stream);
+    DslashArgs a = {};
+    a.prec = prec;
+    a.fat = fat;
+    a.lng = lng;
+    a.c3 = c_naik;
+    a.out_parity = 1;
+    a.in = in;
+    a.out = tmp_odd;
+    a.epi = EPI_PLAIN;
+    if ((st = launch_dslash(l, a, s))) return st;
+    // normal epilogue without CG state (S = NULL): no reduction is formed
+    a.out_parity = 0;
+    a.in = tmp_odd;
+    a.out = out;
+    a.epi = EPI_NORMAL;
+    a.q = in;
+    a.m2 = mass * mass;
+    return launch_dslash(l, a, s);
+}
+
+}  // extern "C"

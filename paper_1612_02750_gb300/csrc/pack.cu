@@ -1,0 +1,268 @@
+// pack.cu -- conversions between the canonical lexicographic layouts and the
+// internal even-odd structure-of-arrays layouts, and FP64 <-> FP32 copies.
+#include "qex_kernels.cuh"
+
+namespace qex {
+
+// Write matrix m (18 reals, element c = 3a+b as re,im) into block (p,mu).
+__device__ __forceinline__ void put_link(double *base, size_t vh, int blk, int i, const double *m) {
+    double2 *b = reinterpret_cast<double2 *>(base) + (size_t)blk * 9 * vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) b[c * vh] = make_double2(m[2 * c], m[2 * c + 1]);
+}
+
+__device__ __forceinline__ void put_link(float *base, size_t vh, int blk, int i, const double *m) {
+    float *bb = base + (size_t)blk * 18 * vh;
+    float4 *b4 = reinterpret_cast<float4 *>(bb) + i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        b4[q * vh] = make_float4((float)m[4 * q], (float)m[4 * q + 1], (float)m[4 * q + 2], (float)m[4 * q + 3]);
+    reinterpret_cast<float2 *>(bb + 16 * vh)[i] = make_float2((float)m[16], (float)m[17]);
+}
+
+__device__ __forceinline__ void get_link(const double *base, size_t vh, int blk, int i, double *m) {
+    const double2 *b = reinterpret_cast<const double2 *>(base) + (size_t)blk * 9 * vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        double2 v = b[c * vh];
+        m[2 * c] = v.x;
+        m[2 * c + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ void get_link(const float *base, size_t vh, int blk, int i, double *m) {
+    const float *bb = base + (size_t)blk * 18 * vh;
+    const float4 *b4 = reinterpret_cast<const float4 *>(bb) + i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float4 v = b4[q * vh];
+        m[4 * q] = v.x;
+        m[4 * q + 1] = v.y;
+        m[4 * q + 2] = v.z;
+        m[4 * q + 3] = v.w;
+    }
+    float2 v = reinterpret_cast<const float2 *>(bb + 16 * vh)[i];
+    m[16] = v.x;
+    m[17] = v.y;
+}
+
+__device__ __forceinline__ void put_vec(double *base, size_t vh, int i, const double *v) {
+    double2 *b = reinterpret_cast<double2 *>(base) + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b[a * vh] = make_double2(v[2 * a], v[2 * a + 1]);
+}
+
+__device__ __forceinline__ void put_vec(float *base, size_t vh, int i, const double *v) {
+    reinterpret_cast<float4 *>(base)[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    reinterpret_cast<float2 *>(base + 4 * vh)[i] = make_float2((float)v[4], (float)v[5]);
+}
+
+__device__ __forceinline__ void get_vec(const double *base, size_t vh, int i, double *v) {
+    const double2 *b = reinterpret_cast<const double2 *>(base) + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double2 t = b[a * vh];
+        v[2 * a] = t.x;
+        v[2 * a + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ void get_vec(const float *base, size_t vh, int i, double *v) {
+    float4 t = reinterpret_cast<const float4 *>(base)[i];
+    float2 u = reinterpret_cast<const float2 *>(base + 4 * vh)[i];
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+    v[4] = u.x;
+    v[5] = u.y;
+}
+
+// blockIdx.y = p*4 + mu; one thread per site of parity p.
+template <typename R>
+__global__ void pack_links_kernel(Geom g, const double *__restrict__ lex, R *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    int blk = blockIdx.y, p = blk >> 2, mu = blk & 3;
+    Site s = site_of(g, p, i);
+    const double *src = lex + ((size_t)s.lex * 4 + mu) * 18;
+    double m[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) m[k] = src[k];
+    put_link(out, g.vh, blk, i, m);
+}
+
+template <typename R>
+__global__ void unpack_links_kernel(Geom g, const R *__restrict__ in, double *__restrict__ lex) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    int blk = blockIdx.y, p = blk >> 2, mu = blk & 3;
+    Site s = site_of(g, p, i);
+    double m[18];
+    get_link(in, g.vh, blk, i, m);
+    double *dst = lex + ((size_t)s.lex * 4 + mu) * 18;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) dst[k] = m[k];
+}
+
+template <typename RI, typename RO>
+__global__ void convert_links_kernel(int vh, const RI *__restrict__ in, RO *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    double m[18];
+    get_link(in, vh, blockIdx.y, i, m);
+    put_link(out, vh, blockIdx.y, i, m);
+}
+
+template <typename R>
+__global__ void pack_field_kernel(Geom g, int p, const double *__restrict__ lex, R *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    Site s = site_of(g, p, i);
+    const double *src = lex + (size_t)s.lex * 6;
+    double v[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = src[k];
+    put_vec(out, g.vh, i, v);
+}
+
+template <typename R>
+__global__ void unpack_field_kernel(Geom g, int p, const R *__restrict__ in, double *__restrict__ lex) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    Site s = site_of(g, p, i);
+    double v[6];
+    get_vec(in, g.vh, i, v);
+    double *dst = lex + (size_t)s.lex * 6;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dst[k] = v[k];
+}
+
+template <typename RI, typename RO>
+__global__ void convert_field_kernel(int vh, const RI *__restrict__ in, RO *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    double v[6];
+    get_vec(in, vh, i, v);
+    put_vec(out, vh, i, v);
+}
+
+static qex_status check_ptrs(const void *a, const void *b) {
+    if (!a || !b) {
+        set_error("field/link pointer is NULL");
+        return QEX_ERR_ARG;
+    }
+    if (!aligned16(a) || !aligned16(b)) {
+        set_error("field/link pointers must be 16-byte aligned");
+        return QEX_ERR_ALIGN;
+    }
+    return QEX_OK;
+}
+
+}  // namespace qex
+
+using namespace qex;
+
+extern "C" {
+
+qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *lex_links, void *internal,
+                          void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec)) || (st = check_ptrs(lex_links, internal))) return st;
+    dim3 grid(blocks_for(lat->vh), 8);
+    if (prec == QEX_F64)
+        pack_links_kernel<double><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, lex_links, (double *)internal);
+    else
+        pack_links_kernel<float><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, lex_links, (float *)internal);
+    QEX_CHECK_LAUNCH("pack_links_kernel");
+    return QEX_OK;
+}
+
+qex_status qex_unpack_links(const qex_lattice *lat, qex_prec prec, const void *internal, double *lex_links,
+                            void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec)) || (st = check_ptrs(lex_links, internal))) return st;
+    dim3 grid(blocks_for(lat->vh), 8);
+    if (prec == QEX_F64)
+        unpack_links_kernel<double><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, (const double *)internal, lex_links);
+    else
+        unpack_links_kernel<float><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, (const float *)internal, lex_links);
+    QEX_CHECK_LAUNCH("unpack_links_kernel");
+    return QEX_OK;
+}
+
+qex_status qex_pack_field(const qex_lattice *lat, qex_prec prec, int parity, const double *lex_field, void *half,
+                          void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec)) || (st = check_ptrs(lex_field, half))) return st;
+    if (parity != 0 && parity != 1) {
+        set_error("parity must be 0 or 1");
+        return QEX_ERR_ARG;
+    }
+    int nb = blocks_for(lat->vh);
+    if (prec == QEX_F64)
+        pack_field_kernel<double><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, lex_field, (double *)half);
+    else
+        pack_field_kernel<float><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, lex_field, (float *)half);
+    QEX_CHECK_LAUNCH("pack_field_kernel");
+    return QEX_OK;
+}
+
+qex_status qex_unpack_field(const qex_lattice *lat, qex_prec prec, int parity, const void *half, double *lex_field,
+                            void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec)) || (st = check_ptrs(lex_field, half))) return st;
+    if (parity != 0 && parity != 1) {
+        set_error("parity must be 0 or 1");
+        return QEX_ERR_ARG;
+    }
+    int nb = blocks_for(lat->vh);
+    if (prec == QEX_F64)
+        unpack_field_kernel<double><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const double *)half, lex_field);
+    else
+        unpack_field_kernel<float><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const float *)half, lex_field);
+    QEX_CHECK_LAUNCH("unpack_field_kernel");
+    return QEX_OK;
+}
+
+qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to, void *out,
+                             void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(from)) || (st = check_prec(to)) || (st = check_ptrs(in, out)))
+        return st;
+    dim3 grid(blocks_for(lat->vh), 8);
+    cudaStream_t s = as_stream(stream);
+    int vh = (int)lat->vh;
+    if (from == QEX_F64 && to == QEX_F32)
+        convert_links_kernel<double, float><<<grid, kBlock, 0, s>>>(vh, (const double *)in, (float *)out);
+    else if (from == QEX_F32 && to == QEX_F64)
+        convert_links_kernel<float, double><<<grid, kBlock, 0, s>>>(vh, (const float *)in, (double *)out);
+    else if (from == QEX_F64)
+        convert_links_kernel<double, double><<<grid, kBlock, 0, s>>>(vh, (const double *)in, (double *)out);
+    else
+        convert_links_kernel<float, float><<<grid, kBlock, 0, s>>>(vh, (const float *)in, (float *)out);
+    QEX_CHECK_LAUNCH("convert_links_kernel");
+    return QEX_OK;
+}
+
+qex_status qex_convert_field(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to, void *out,
+                             void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(from)) || (st = check_prec(to)) || (st = check_ptrs(in, out)))
+        return st;
+    int nb = blocks_for(lat->vh);
+    cudaStream_t s = as_stream(stream);
+    int vh = (int)lat->vh;
+    if (from == QEX_F64 && to == QEX_F32)
+        convert_field_kernel<double, float><<<nb, kBlock, 0, s>>>(vh, (const double *)in, (float *)out);
+    else if (from == QEX_F32 && to == QEX_F64)
+        convert_field_kernel<float, double><<<nb, kBlock, 0, s>>>(vh, (const float *)in, (double *)out);
+    else if (from == QEX_F64)
+        convert_field_kernel<double, double><<<nb, kBlock, 0, s>>>(vh, (const double *)in, (double *)out);
+    else
+        convert_field_kernel<float, float><<<nb, kBlock, 0, s>>>(vh, (const float *)in, (float *)out);
+    QEX_CHECK_LAUNCH("convert_field_kernel");
+    return QEX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+// qex_common.cuh -- shared device/host helpers of libqex_gpu: lattice
+// geometry (even-odd indexing, neighbours, staggered phases, boundary signs),
+// internal field/link layouts, complex colour algebra, deterministic block
+// reductions and the error plumbing of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/qex_gpu.h"
+
+#define QEX_HD __host__ __device__ __forceinline__
+
+namespace qex {
+
+// ----------------------------------------------------------------- errors
+
+void set_error(const char *fmt, ...);
+qex_status cuda_fail(cudaError_t e, const char *what);
+
+#define QEX_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return ::qex::cuda_fail(_e, #call);  \
+    } while (0)
+
+#define QEX_CHECK_LAUNCH(what)                                      \
+    do {                                                            \
+        cudaError_t _e = cudaGetLastError();                        \
+        if (_e != cudaSuccess) return ::qex::cuda_fail(_e, what);   \
+    } while (0)
+
+// ------------------------------------------------------- fast division
+// Division by a run-time invariant divisor d in [1, 2^31) through a
+// multiply-high, exact for every 32-bit dividend (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Fig. 4.1).
+struct FastDiv {
+    uint32_t d, m;
+    uint32_t s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;  // l = ceil(log2 d)
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+QEX_HD uint32_t fd_div(const FastDiv &f, uint32_t n) {
+#ifdef __CUDA_ARCH__
+    uint32_t t1 = __umulhi(f.m, n);
+#else
+    uint32_t t1 = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+    return (t1 + ((n - t1) >> f.s1)) >> f.s2;
+}
+
+// ------------------------------------------------------------ geometry
+// Site lex = x + Lx*(y + Ly*(z + Lz*t)).  Lx is even, so the sites of one
+// parity are exactly the lex values {2i, 2i+1} with one member chosen by
+// parity; i = lex >> 1 is their rank within the parity (the even-odd index).
+struct Geom {
+    int L[4];        // extents x, y, z, t
+    int stride[4];   // lex strides 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int vh;          // V / 2
+    int antiperiodic;
+    FastDiv div_xh;  // Lx / 2
+    FastDiv div_y;   // Ly
+    FastDiv div_z;   // Lz
+};
+
+struct Site {
+    int c[4];   // coordinates x, y, z, t
+    int lex;
+};
+
+// Coordinates of the i-th site of parity p.
+QEX_HD Site site_of(const Geom &g, int p, int i) {
+    uint32_t r1 = fd_div(g.div_xh, (uint32_t)i);
+    int xh = i - (int)r1 * (g.L[0] >> 1);
+    uint32_t r2 = fd_div(g.div_y, r1);
+    int y = (int)r1 - (int)r2 * g.L[1];
+    uint32_t t = fd_div(g.div_z, r2);
+    int z = (int)r2 - (int)t * g.L[2];
+    int bit = (p + y + z + (int)t) & 1;
+    Site s;
+    s.c[0] = 2 * xh + bit;
+    s.c[1] = y;
+    s.c[2] = z;
+    s.c[3] = (int)t;
+    s.lex = 2 * i + bit;
+    return s;
+}
+
+// Even-odd index (within the neighbour's parity) of site + k*mu_hat,
+// 0 < |k| < L[mu] (a single periodic wrap).
+QEX_HD int hop_index(const Geom &g, const Site &s, int mu, int k) {
+    int c = s.c[mu] + k;
+    int lex = s.lex + k * g.stride[mu];
+    if (c >= g.L[mu]) lex -= g.L[mu] * g.stride[mu];
+    if (c < 0) lex += g.L[mu] * g.stride[mu];
+    return lex >> 1;
+}
+
+// Staggered phase eta_mu(x) as a 0/1 sign bit: (-1)^(x_0 + ... + x_{mu-1}).
+QEX_HD int eta_bit(const Site &s, int mu) {
+    int e = 0;
+    for (int nu = 0; nu < mu; ++nu) e += s.c[nu];
+    return e & 1;
+}
+
+// Antiperiodic-time sign bit of the k-step link leaving the site along +mu:
+// set when mu = t and the hop crosses t = Lt-1 -> 0 (k < Lt, one crossing).
+QEX_HD int bc_bit_fwd(const Geom &g, const Site &s, int mu, int k) {
+    return (mu == 3 && g.antiperiodic && s.c[3] + k >= g.L[3]) ? 1 : 0;
+}
+// Sign bit of the k-step link arriving at the site from site - k*mu_hat.
+QEX_HD int bc_bit_bwd(const Geom &g, const Site &s, int mu, int k) {
+    return (mu == 3 && g.antiperiodic && s.c[3] - k < 0) ? 1 : 0;
+}
+
+Geom make_geom(const int dims[4], int antiperiodic);
+
+// --------------------------------------------------------- layouts
+// Internal link set: block (p, mu) holds the Vh links U_mu(x) of the sites x
+// of parity p, as planes over sites.
+//   F64: 9 planes of double2 (element c = 3a + b); block size 9*Vh double2.
+//   F32: 4 planes of float4 (elements {0,1},{2,3},{4,5},{6,7}) then 1 plane
+//        of float2 (element 8); block size 18*Vh floats.
+// Half field (Vh sites of one parity):
+//   F64: 3 planes of double2 (colour a);  F32: float4 plane (colours 0, 1)
+//   then float2 plane (colour 2).
+template <typename R> struct Cplx { R re, im; };
+
+template <typename R> struct Vec3 { Cplx<R> c[3]; };
+template <typename R> struct Mat3 { Cplx<R> e[9]; };
+
+__device__ __forceinline__ Mat3<double> load_link(const double *base, size_t vh, int p, int mu, int i) {
+    const double2 *b = reinterpret_cast<const double2 *>(base) + (size_t)(p * 4 + mu) * 9 * vh + i;
+    Mat3<double> m;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        double2 v = __ldg(b + c * vh);
+        m.e[c].re = v.x;
+        m.e[c].im = v.y;
+    }
+    return m;
+}
+
+__device__ __forceinline__ Mat3<float> load_link(const float *base, size_t vh, int p, int mu, int i) {
+    const float *blk = base + (size_t)(p * 4 + mu) * 18 * vh;
+    const float4 *b4 = reinterpret_cast<const float4 *>(blk) + i;
+    Mat3<float> m;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float4 v = __ldg(b4 + q * vh);
+        m.e[2 * q].re = v.x;
+        m.e[2 * q].im = v.y;
+        m.e[2 * q + 1].re = v.z;
+        m.e[2 * q + 1].im = v.w;
+    }
+    float2 v = __ldg(reinterpret_cast<const float2 *>(blk + 16 * vh) + i);
+    m.e[8].re = v.x;
+    m.e[8].im = v.y;
+    return m;
+}
+
+__device__ __forceinline__ Vec3<double> load_vec(const double *base, size_t vh, int i) {
+    const double2 *b = reinterpret_cast<const double2 *>(base) + i;
+    Vec3<double> v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double2 t = __ldg(b + a * vh);
+        v.c[a].re = t.x;
+        v.c[a].im = t.y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ Vec3<float> load_vec(const float *base, size_t vh, int i) {
+    float4 t = __ldg(reinterpret_cast<const float4 *>(base) + i);
+    float2 u = __ldg(reinterpret_cast<const float2 *>(base + 4 * vh) + i);
+    Vec3<float> v;
+    v.c[0].re = t.x;
+    v.c[0].im = t.y;
+    v.c[1].re = t.z;
+    v.c[1].im = t.w;
+    v.c[2].re = u.x;
+    v.c[2].im = u.y;
+    return v;
+}
+
+__device__ __forceinline__ void store_vec(double *base, size_t vh, int i, const Vec3<double> &v) {
+    double2 *b = reinterpret_cast<double2 *>(base) + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b[a * vh] = make_double2(v.c[a].re, v.c[a].im);
+}
+
+__device__ __forceinline__ void store_vec(float *base, size_t vh, int i, const Vec3<float> &v) {
+    reinterpret_cast<float4 *>(base)[i] = make_float4(v.c[0].re, v.c[0].im, v.c[1].re, v.c[1].im);
+    reinterpret_cast<float2 *>(base + 4 * vh)[i] = make_float2(v.c[2].re, v.c[2].im);
+}
+
+// ----------------------------------------------------- colour algebra
+// acc += sgn * (M v), sgn = +1 or -1.
+template <typename R>
+__device__ __forceinline__ void acc_mv(Vec3<R> &acc, R sgn, const Mat3<R> &m, const Vec3<R> &v) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R re = m.e[3 * a].re * v.c[0].re;
+        R im = m.e[3 * a].re * v.c[0].im;
+        re = fma(-m.e[3 * a].im, v.c[0].im, re);
+        im = fma(m.e[3 * a].im, v.c[0].re, im);
+#pragma unroll
+        for (int b = 1; b < 3; ++b) {
+            re = fma(m.e[3 * a + b].re, v.c[b].re, re);
+            re = fma(-m.e[3 * a + b].im, v.c[b].im, re);
+            im = fma(m.e[3 * a + b].re, v.c[b].im, im);
+            im = fma(m.e[3 * a + b].im, v.c[b].re, im);
+        }
+        acc.c[a].re = fma(sgn, re, acc.c[a].re);
+        acc.c[a].im = fma(sgn, im, acc.c[a].im);
+    }
+}
+
+// acc += sgn * (M^+ v).
+template <typename R>
+__device__ __forceinline__ void acc_mdv(Vec3<R> &acc, R sgn, const Mat3<R> &m, const Vec3<R> &v) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R re = m.e[a].re * v.c[0].re;
+        R im = m.e[a].re * v.c[0].im;
+        re = fma(m.e[a].im, v.c[0].im, re);
+        im = fma(-m.e[a].im, v.c[0].re, im);
+#pragma unroll
+        for (int b = 1; b < 3; ++b) {
+            re = fma(m.e[3 * b + a].re, v.c[b].re, re);
+            re = fma(m.e[3 * b + a].im, v.c[b].im, re);
+            im = fma(m.e[3 * b + a].re, v.c[b].im, im);
+            im = fma(-m.e[3 * b + a].im, v.c[b].re, im);
+        }
+        acc.c[a].re = fma(sgn, re, acc.c[a].re);
+        acc.c[a].im = fma(sgn, im, acc.c[a].im);
+    }
+}
+
+// --------------------------------------------------- block reductions
+// Deterministic: a fixed shuffle tree within each warp, then warp 0 reduces
+// the per-warp values in index order.  Requires blockDim.x % 32 == 0, <= 1024.
+__device__ __forceinline__ double block_sum(double v, double *smem /* >= 32 */) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) smem[w] = v;
+    __syncthreads();
+    double s = 0;
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        s = lane < nw ? smem[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// Sum of partial[0..n) by one block in a fixed order (valid in thread 0).
+// Reads bypass L1 (the partials were written by other blocks).
+__device__ __forceinline__ double block_sum_partials(const double *partial, int n, double *smem) {
+    double s = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += __ldcg(partial + k);
+    return block_sum(s, smem);
+}
+
+// ------------------------------------------------------- lattice object
+struct CgScalars;
+
+}  // namespace qex
+
+struct qex_lattice {
+    int dims[4];
+    int antiperiodic;
+    int64_t volume;
+    int64_t vh;
+    qex::Geom geom;
+    int device;
+    // scratch owned by the library
+    double *partials;          // per-block partial sums (max over kernels)
+    int partials_len;
+    unsigned int *counter;     // last-block counters (zero between calls)
+    double *red_out;           // small result area for reductions
+    qex::CgScalars *scalars;   // CG state (device)
+    qex::CgScalars *scalars_host;   // pinned mirror, readback slot 0
+    qex::CgScalars *scalars_host2;  // pinned readback slot 1
+    void *work;                // CG work vectors
+    size_t work_bytes;
+    cudaEvent_t ev0, ev1;
+};
+
+namespace qex {
+
+qex_status ensure_scratch(qex_lattice *lat);
+qex_status ensure_work(qex_lattice *lat, size_t bytes);
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+qex_status check_lattice(const qex_lattice *lat);
+qex_status check_prec(qex_prec prec);
+
+constexpr int kBlock = 256;  // threads per block of the site kernels
+
+inline int blocks_for(int64_t n, int bs = kBlock) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace qex

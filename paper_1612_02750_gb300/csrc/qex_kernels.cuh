@@ -1,0 +1,79 @@
+// qex_kernels.cuh -- device-resident CG state and the host launchers that the
+// translation units of libqex_gpu share.
+#pragma once
+
+#include "qex_common.cuh"
+
+namespace qex {
+
+// CG scalars live in device memory so that an iteration needs no host round
+// trip; the last block of each reducing kernel updates them (fixed-order sum
+// of the per-block partials, so results are bit-reproducible).
+struct CgScalars {
+    double rr;        // ||r||^2 of the iterated residual (FP64 accumulation)
+    double pAp;       // Re <p, A p>
+    double alpha;     // rr / pAp
+    double beta;      // rr_new / rr
+    double bb;        // ||b||^2
+    double tol2;      // tol^2
+    double stop2;     // tol^2 * bb
+    double delta2;    // reliable-update threshold factor delta^2 (0: only at convergence)
+    double rmax2;     // max ||r||^2 since the last reliable update
+    double true_rr;   // ||b - A x||^2 from the last FP64 recomputation
+    int iters;        // completed iterations
+    int maxiter;
+    int done;         // true residual met tol
+    int need_ru;      // iterated residual calls for an FP64 recomputation
+    int halt;         // done | need_ru | error: iteration kernels return at once
+    int error;        // 1: NaN/Inf in a reduction, 2: <p, Ap> <= 0
+    int reliable_updates;
+    int pad;
+};
+
+// Epilogues of the Dslash kernel.
+enum Epilogue {
+    EPI_PLAIN = 0,   // out = D in
+    EPI_NORMAL = 1,  // out = m^2 q - D in; Re<q, out> -> pAp, alpha   (CG: q = p)
+    EPI_RESID = 2    // out = b - m^2 q + D in; ||out||^2 -> true_rr, flags (CG: q = x)
+};
+
+struct DslashArgs {
+    qex_prec prec;
+    const void *fat;
+    const void *lng;     // NULL: no Naik term
+    double c3;
+    int out_parity;
+    const void *in;
+    void *out;
+    int epi;
+    const void *q;       // EPI_NORMAL / EPI_RESID
+    const double *b;     // EPI_RESID (FP64 half field)
+    double m2;
+    CgScalars *S;        // EPI_NORMAL / EPI_RESID / halt check
+    int check_halt;
+};
+
+qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
+
+// BLAS-1 pieces of the CG iteration (grid-stride, fixed grid per lattice).
+// x += alpha p; r -= alpha ap; ||r||^2 -> S (rr, beta, flags).
+qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, const void *p,
+                            const void *ap, CgScalars *S, cudaStream_t st);
+// p = r + beta p  (halt-checked when check_halt).
+qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *p, CgScalars *S,
+                           int check_halt, cudaStream_t st);
+// x64 += (double) xh32; xh32 = 0.
+qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st);
+// r32 = (float) r64; p32 = r32 + beta p32.
+qex_status launch_lower_r_update_p(qex_lattice *lat, const double *r64, float *r32, float *p32,
+                                   CgScalars *S, cudaStream_t st);
+// ||f||^2 -> *out (FP64, fixed order); if S, also S->bb and S->stop2.
+qex_status launch_norm2(qex_lattice *lat, qex_prec prec, const void *f, double *out, CgScalars *S,
+                        cudaStream_t st);
+// <a, b> -> out[0..1].
+qex_status launch_dot(qex_lattice *lat, qex_prec prec, const void *a, const void *b, double *out,
+                      cudaStream_t st);
+
+int blas_blocks(const qex_lattice *lat);
+
+}  // namespace qex

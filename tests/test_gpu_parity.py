@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (norm-wise ||gpu - oracle|| / ||oracle|| per field): 1e-13 for
+FP64, 1e-5 for FP32 (inputs rounded to FP32 on the device, oracle in FP64 on
+the unrounded inputs).  Index work (neighbour tables, packing) is bit-exact.
+Lattices span several 256-site blocks and a ragged tail.
+"""
+
+import numpy as np
+import pytest
+
+import fieldgen as fg
+
+pytestmark = pytest.mark.gpu
+
+C3 = -1.0 / 24.0
+TOL = {"f64": 1e-13, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_02750_gb300 import build
+
+    build.build()
+    import paper_1612_02750_gb300 as mod
+
+    mod.load()
+    return mod
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+class Setup:
+    """Packed links (F64 and F32) of one seeded input."""
+
+    def __init__(self, q, dims, naik, seed=1, fat="haar", antiperiodic=True, a=0.3):
+        self.q = q
+        self.dims = dims
+        s = fg.rng_streams(seed)
+        self.u = fg.random_links(dims, fat, s["links"], a)
+        self.w = fg.random_links(dims, "gauss3", s["long_links"]) if naik else None
+        self.psi = fg.gaussian_field(s["source"], dims)
+        self.ap = antiperiodic
+        self.lat = q.Lattice(dims, antiperiodic)
+        self.fat = {"f64": q.qex_pack_links(self.lat, "f64", dev(self.u))}
+        self.fat["f32"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32")
+        self.lng = {"f64": None, "f32": None}
+        if naik:
+            self.lng["f64"] = q.qex_pack_links(self.lat, "f64", dev(self.w))
+            self.lng["f32"] = q.qex_pack_links(self.lat, "f32", dev(self.w))
+
+    def half(self, prec, parity, field):
+        return self.q.qex_pack_field(self.lat, prec, parity, dev(field))
+
+    def full(self, prec, parity, half):
+        return host(self.q.qex_unpack_field(self.lat, prec, parity, half))
+
+
+SHAPES = [(4, 4, 4, 4), (6, 4, 4, 10), (8, 4, 6, 4), (8, 8, 8, 12), (16, 8, 8, 8), (4, 6, 10, 8)]
+
+
+@pytest.mark.parametrize("dims", SHAPES + [(2, 4, 2, 6)])
+def test_neighbor_table_device_bit_exact(q, oracle_mod, dims):
+    lat = q.Lattice(dims)
+    for p in (0, 1):
+        for mu in range(4):
+            for hop in ((1, -1, 3, -3) if dims[mu] >= 4 else (1, -1)):
+                got = host(q.qex_neighbor_table_device(lat, p, mu, hop))
+                assert np.array_equal(got, oracle_mod.neighbor_table(dims, p, mu, hop))
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 10)])
+def test_pack_roundtrip_bit_exact(q, dims):
+    s = fg.rng_streams(3)
+    u = fg.random_links(dims, "haar", s["links"])
+    lat = q.Lattice(dims)
+    for prec, cast in (("f64", np.complex128), ("f32", np.complex64)):
+        back = host(q.qex_unpack_links(lat, prec, q.qex_pack_links(lat, prec, dev(u))))
+        assert np.array_equal(back, u.astype(cast).astype(np.complex128))
+        f = fg.gaussian_field(s["source"], dims)
+        ev = fg.even_mask(dims)
+        for p in (0, 1):
+            half = q.qex_pack_field(lat, prec, p, dev(f))
+            out = dev(np.full_like(f, 7.0))
+            q.qex_unpack_field(lat, prec, p, half, out)
+            out = host(out)
+            mine = ev if p == 0 else ~ev
+            assert np.array_equal(out[mine], f.astype(cast).astype(np.complex128)[mine])
+            assert np.all(out[~mine] == 7.0)
+    l32 = q.qex_pack_links(lat, "f32", dev(u))
+    l64 = q.qex_convert_links(lat, "f32", l32, "f64")
+    assert np.array_equal(host(q.qex_unpack_links(lat, "f64", l64)), u.astype(np.complex64).astype(np.complex128))
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("naik", [False, True])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dslash_parity(q, oracle_mod, dims, naik, prec):
+    S = Setup(q, dims, naik, seed=21)
+    for ap in (True, False):
+        if not ap:
+            S = Setup(q, dims, naik, seed=21, antiperiodic=False)
+        for out_p in (0, 1):
+            inp = S.half(prec, 1 - out_p, S.psi)
+            got = S.full(prec, out_p, q.qex_dslash(S.lat, prec, S.fat[prec], S.lng[prec], C3, out_p, inp))
+            ref = oracle_mod.dslash_parity(dims, S.u, S.psi, out_p, S.w, C3, ap)
+            mask = fg.even_mask(dims) if out_p == 0 else ~fg.even_mask(dims)
+            assert relerr(got[mask], ref[mask]) <= TOL[prec], (ap, out_p)
+
+
+def test_dslash_exp_links_and_unit_links(q, oracle_mod):
+    dims = (8, 6, 4, 10)
+    for fat in ("exp", "unit"):
+        S = Setup(q, dims, True, seed=4, fat=fat)
+        inp = S.half("f64", 1, S.psi)
+        got = S.full("f64", 0, q.qex_dslash(S.lat, "f64", S.fat["f64"], S.lng["f64"], C3, 0, inp))
+        ref = oracle_mod.dslash_parity(dims, S.u, S.psi, 0, S.w, C3, True)
+        ev = fg.even_mask(dims)
+        assert relerr(got[ev], ref[ev]) <= 1e-13
+
+
+@pytest.mark.parametrize("naik", [False, True])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_normal_op_parity(q, oracle_mod, naik, prec):
+    dims = (8, 4, 6, 10)
+    S = Setup(q, dims, naik, seed=22)
+    m = 0.07
+    x = S.psi.copy()
+    ev = fg.even_mask(dims)
+    x[~ev] = 0
+    got = S.full(prec, 0, q.qex_normal_op(S.lat, prec, S.fat[prec], S.lng[prec], C3, m, S.half(prec, 0, x)))
+    ref = oracle_mod.normal_op(dims, S.u, x, m, S.w, C3)
+    assert relerr(got[ev], ref[ev]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_norm2_and_dot(q, prec):
+    dims = (8, 8, 6, 10)
+    lat = q.Lattice(dims)
+    s = fg.rng_streams(8)
+    a, b = fg.gaussian_field(s["source"], dims), fg.gaussian_field(s["chi"], dims)
+    ev = fg.even_mask(dims)
+    ha, hb = q.qex_pack_field(lat, prec, 0, dev(a)), q.qex_pack_field(lat, prec, 0, dev(b))
+    cast = np.complex128 if prec == "f64" else np.complex64
+    ae, be = a[ev].astype(cast).astype(np.complex128), b[ev].astype(cast).astype(np.complex128)
+    n1 = host(q.qex_norm2(lat, prec, ha))[0]
+    assert n1 == pytest.approx(np.vdot(ae, ae).real, rel=1e-13 if prec == "f64" else 1e-6)
+    d = host(q.qex_dot(lat, prec, ha, hb))
+    ref = np.vdot(ae, be)
+    assert abs(complex(d[0], d[1]) - ref) <= (1e-12 if prec == "f64" else 1e-5) * np.sqrt(n1 * np.vdot(be, be).real)
+    # fixed-order reductions: bitwise reproducible
+    assert host(q.qex_norm2(lat, prec, ha))[0] == n1
+    assert np.array_equal(host(q.qex_dot(lat, prec, ha, hb)), d)
+
+
+def _cg(q, S, inner, m, b_full, tol=1e-10, maxiter=20000, delta=0.1, x0=None):
+    import torch
+
+    b = S.half("f64", 0, b_full)
+    x = S.half("f64", 0, x0) if x0 is not None else torch.zeros_like(b)
+    st, stats = q.qex_cg(S.lat, inner, S.fat["f64"], S.lng["f64"], S.fat["f32"], S.lng["f32"], C3, m, b, x,
+                         tol=tol, maxiter=maxiter, delta=delta, check=False)
+    return st, stats, S.full("f64", 0, x)
+
+
+@pytest.mark.parametrize("naik", [False, True])
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_cg_parity(q, oracle_mod, naik, inner):
+    dims = (8, 8, 4, 8)
+    m = 0.1
+    S = Setup(q, dims, naik, seed=23)
+    b = S.psi.copy()
+    b[~fg.even_mask(dims)] = 0
+    st, stats, x = _cg(q, S, inner, m, b)
+    assert st == 0 and stats["converged"], stats
+    tr = oracle_mod.true_residual(dims, S.u, b, x, m, S.w, C3)
+    assert tr <= 1.05e-10 and stats["true_rel_resid"] == pytest.approx(tr, rel=1e-3, abs=1e-13)
+    xr, ok, it, _ = oracle_mod.cg(dims, S.u, b, m, S.w, C3, tol=1e-13, maxiter=50000)
+    assert ok
+    ev = fg.even_mask(dims)
+    assert relerr(x[ev], xr[ev]) <= 1e-7
+    if inner == "f32":
+        assert stats["reliable_updates"] >= 1
+
+
+def test_cg_workload_4x4_fp64_matches_oracle_iterations(q, oracle_mod):
+    """4^4, Haar links, m = 0.1: FP64 CG reaches 1e-10 with the oracle's
+    iteration count up to rounding-driven differences."""
+    wl = fg.workload("cfg4x4")
+    dims = wl["dims"]
+    u, _, b = fg.make_inputs(dims, "haar", False, wl["seed"])
+    S = Setup(q, dims, False, seed=wl["seed"])  # same streams: S.u is u
+    assert np.array_equal(S.u, u)
+    st, stats, x = _cg(q, S, "f64", wl["mass"], b)
+    assert st == 0
+    tr = oracle_mod.true_residual(dims, u, b, x, wl["mass"])
+    assert tr <= 1.05e-10
+    _, ok, it, _ = oracle_mod.cg(dims, u, b, wl["mass"], tol=1e-10)
+    assert abs(stats["iters"] - it) <= max(5, it // 10)
+
+
+def test_cg_edge_cases(q, oracle_mod):
+    import torch
+
+    dims = (4, 4, 4, 8)
+    S = Setup(q, dims, True, seed=24)
+    zero = np.zeros_like(S.psi)
+    st, stats, x = _cg(q, S, "f32", 0.1, zero, x0=S.psi)
+    assert st == 0 and stats["converged"] and not x.any()
+    b = S.psi.copy()
+    b[~fg.even_mask(dims)] = 0
+    st, stats, x = _cg(q, S, "f64", 0.1, b, maxiter=2)
+    assert st == 5 and stats["iters"] == 2 and not stats["converged"]
+    st, stats, x = _cg(q, S, "f32", 0.1, b, maxiter=0)
+    assert st == 5
+    bad = b.copy()
+    bad[0, 0, 0, 0, 1] = np.nan
+    st, stats, x = _cg(q, S, "f64", 0.1, bad)
+    assert st == 7
+    # warm start from the converged solution: at most one iteration
+    st, stats, x = _cg(q, S, "f64", 0.1, b, tol=1e-10)
+    assert st == 0
+    st2, stats2, x2 = _cg(q, S, "f32", 0.1, b, tol=1e-9, x0=x)
+    assert st2 == 0 and stats2["iters"] <= 1
+    # bitwise reproducible solve
+    _, _, xa = _cg(q, S, "f32", 0.1, b)
+    _, _, xb = _cg(q, S, "f32", 0.1, b)
+    assert np.array_equal(xa, xb)
+    torch.cuda.synchronize()
+
+
+def test_device_argument_errors(q):
+    import torch
+
+    dims = (4, 4, 2, 4)
+    lat = q.Lattice(dims)
+    f = q.zeros_field(lat, "f64")
+    links = q.empty_links(lat, "f64")
+    lng = q.empty_links(lat, "f64")
+    with pytest.raises(q.QexError) as e:
+        q.qex_dslash(lat, "f64", links, lng, C3, 0, f)  # Naik on extent 2
+    assert e.value.status == 2
+    raw = torch.zeros(f.numel() + 2, dtype=torch.float64, device="cuda")
+    mis = raw[1:1 + f.numel()]
+    with pytest.raises(q.QexError) as e:
+        q.qex_dslash(lat, "f64", links, None, 0.0, 0, mis, q.empty_field(lat, "f64"))
+    assert e.value.status == 3
+    with pytest.raises(q.QexError) as e:
+        q.qex_dslash(lat, "f64", links, None, 0.0, 0, f, f)
+    assert e.value.status == 1
+    with pytest.raises(q.QexError) as e:
+        q.qex_dslash(lat, "f64", links, None, 0.0, 2, f)
+    assert e.value.status == 1
+
+
+@pytest.mark.slow
+def test_full_size_32_dslash_and_mixed_cg(q, oracle_mod):
+    """The 32^4 workload (links exp(i 0.3 H), m = 0.01) in the launch
+    configuration the benchmark times: full-lattice Dslash parity in both
+    precisions and a mixed-precision solve whose true residual the oracle
+    recomputes."""
+    wl = fg.workload("cfg32")
+    dims = wl["dims"]
+    u, _, b = fg.make_inputs(dims, wl["fat"], False, wl["seed"], wl["a"])
+    lat = q.Lattice(dims)
+    fat64 = q.qex_pack_links(lat, "f64", dev(u))
+    fat32 = q.qex_convert_links(lat, "f64", fat64, "f32")
+    ev = fg.even_mask(dims)
+    for prec, fat in (("f64", fat64), ("f32", fat32)):
+        inp = q.qex_pack_field(lat, prec, 0, dev(b))
+        got = host(q.qex_unpack_field(lat, prec, 1, q.qex_dslash(lat, prec, fat, None, 0.0, 1, inp)))
+        ref = oracle_mod.dslash_parity(dims, u, b, 1, None, 0.0, True)
+        assert relerr(got[~ev], ref[~ev]) <= TOL[prec]
+    bh = q.qex_pack_field(lat, "f64", 0, dev(b))
+    import torch
+
+    x = torch.zeros_like(bh)
+    st, stats = q.qex_cg(lat, "f32", fat64, None, fat32, None, 0.0, wl["mass"], bh, x, tol=1e-10, maxiter=100000)
+    xf = host(q.qex_unpack_field(lat, "f64", 0, x))
+    tr = oracle_mod.true_residual(dims, u, b, xf, wl["mass"])
+    assert st == 0 and tr <= 1.05e-10, (stats, tr)
