@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark: even-odd staggered CG on one GB300 (one JSON line on rank 0).
+
+A step is one pass of the whole path on the 32^4 workload (links
+exp(i 0.3 H), m = 0.01, one Gaussian even-site source): pack the canonical
+FP64 links into the internal layout, round the FP32 copy, pack the source,
+solve (m^2 - D_eo D_oe) x = b by mixed-precision CG (FP32 inner iteration,
+FP64 reliable updates) to a true relative residual of 1e-10, and unpack the
+solution.  ``value`` is solves per second over all ranks with inputs resident
+in HBM; ``e2e`` is the same through ``qex_cg_host`` from page-locked host
+buffers (copies inside the timed region).  Ranks are independent replicas
+(the lattice is not split across GPUs).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s & GFLOP/s vs HBM roofline; CG time to 1e-10 residual, mixed vs FP64"
+WORKLOAD = "cfg32"
+TOL = 1e-10
+DELTA = 0.1
+FLOP_NN = 570          # flops per output site of the one-hop Dslash (8 mat-vecs x 66 + 7 x 6 adds)
+BYTES_NN = {"f64": 1248, "f32": 624}  # 8 links + 8 input vectors once + 1 output vector
+L2_BYTES = 135528448   # sm_103a L2 (cudaDevAttrL2CacheSize on GB300)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dslash-only", action="store_true",
+                    help="profiling case: two FP32 then two FP64 one-hop Dslash launches on the workload, no timing")
+    return ap.parse_args()
+
+
+def workload_desc(wl):
+    lx, ly, lz, lt = wl["dims"]
+    return (f"{lx}x{ly}x{lz}x{lt} staggered, links exp(i {wl['a']} H) SU(3), m={wl['mass']}, "
+            f"1 Gaussian even-site source, mixed-precision CG to true residual {TOL:g}")
+
+
+# ------------------------------------------------------------------ distributed
+
+class Dist:
+    def __init__(self, want_gpu: bool):
+        import torch
+
+        self.rank = int(os.environ.get("RANK", 0))
+        self.world = int(os.environ.get("WORLD_SIZE", 1))
+        self.local = int(os.environ.get("LOCAL_RANK", 0))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            backend = "nccl" if (want_gpu and torch.cuda.is_available()) else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples every 100 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 7:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = sorted({self.NAMES[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------------- helpers
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1612_02750_gb300/csrc/dslash.cu", "paper_1612_02750_gb300/csrc/qex_common.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[kernel_key]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def oracle_iterations(name: str):
+    path = os.path.join(ROOT, "oracle", "workload_solves.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[name]
+        return int(rec["iters"]) if rec.get("converged") else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def oracle_sample(wl, u, b, seconds: float, fp64_iters: int):
+    """Time the oracle's FP64 CG for a bounded number of iterations and scale
+    to one full solve (iterations from the oracle's own converged solve)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.normal_op(wl["dims"], u, b, wl["mass"])
+    t_op = time.perf_counter() - t0
+    n = max(1, int(seconds / max(t_op, 1e-6)) - 2)
+    t0 = time.perf_counter()
+    oracle.cg(wl["dims"], u, b, wl["mass"], tol=TOL, maxiter=n)
+    t = time.perf_counter() - t0
+    iters = oracle_iterations(WORKLOAD) or fp64_iters
+    src = "oracle's converged iteration count" if oracle_iterations(WORKLOAD) else "GPU FP64 iteration count"
+    solve_s = t * (iters + 2) / (n + 2)  # n iterations + initial and final residual
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"oracle FP64 CG, {n} iterations on the full {'x'.join(map(str, wl['dims']))} lattice "
+                      f"({t:.1f} s), scaled to {iters} iterations ({src}) + 2 residual evaluations",
+            "seconds_per_solve": solve_s}
+
+
+def make_inputs(wl):
+    import fieldgen as fg
+
+    u, _, b = fg.make_inputs(wl["dims"], wl["fat"], False, wl["seed"], wl["a"])
+    return u, b
+
+
+# --------------------------------------------------------------------- native
+
+def run_native(args):
+    import torch
+
+    import fieldgen as fg
+    import paper_1612_02750_gb300 as q
+    from paper_1612_02750_gb300 import build as qbuild
+
+    dist = Dist(want_gpu=True)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(dist.local)
+    qbuild.build()
+    q.load()
+    wl = fg.workload(WORKLOAD)
+    dims, mass = wl["dims"], wl["mass"]
+    u, b = make_inputs(wl)
+    lat = q.Lattice(dims, antiperiodic=True)
+    vh = lat.half_volume
+
+    U_h = torch.from_numpy(u).pin_memory()
+    B_h = torch.from_numpy(b).pin_memory()
+    X_h = torch.empty_like(B_h).pin_memory()
+    U_d = U_h.cuda()
+    B_d = B_h.cuda()
+    X_d = torch.zeros_like(B_d)
+    fat64 = q.empty_links(lat, "f64")
+    fat32 = q.empty_links(lat, "f32")
+    bh = q.empty_field(lat, "f64")
+    x = q.empty_field(lat, "f64")
+    stream = torch.cuda.current_stream()
+
+    def step(inner="f32"):
+        q.qex_pack_links(lat, "f64", U_d, fat64)
+        q.qex_convert_links(lat, "f64", fat64, "f32", fat32)
+        q.qex_pack_field(lat, "f64", 0, B_d, bh)
+        x.zero_()
+        _, stats = q.qex_cg(lat, inner, fat64, None, fat32, None, 0.0, mass, bh, x, tol=TOL, maxiter=200000,
+                            delta=DELTA)
+        q.qex_unpack_field(lat, "f64", 0, x, X_d)
+        return stats
+
+    for _ in range(args.warmup):
+        stats = step()
+    clocks = Clocks(torch.cuda.current_device())
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = q.qex_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    all_stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = q.qex_launch_count() - n0
+    clk = clocks.stop()
+    dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = dist.max(ms)
+    value = dist.world * 1000.0 / ms_max
+    mixed = all_stats[-1]
+
+    # FP64 CG on the same inputs (the "mixed vs FP64" half of the metric)
+    torch.cuda.synchronize()
+    f0 = time.perf_counter()
+    st64 = step("f64")
+    torch.cuda.synchronize()
+    fp64_ms = (time.perf_counter() - f0) * 1e3
+
+    # dominant kernel: FP32 one-hop Dslash, timed on its stream (inputs >> L2)
+    def time_dslash(prec, fat, reps=40):
+        inp = q.empty_field(lat, prec).normal_()
+        out = q.empty_field(lat, prec)
+        for _ in range(5):
+            q.qex_dslash(lat, prec, fat, None, 0.0, 1, inp, out)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            q.qex_dslash(lat, prec, fat, None, 0.0, 1, inp, out)
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / reps
+
+    d32 = time_dslash("f32", fat32)
+    d64 = time_dslash("f64", fat64)
+    peak, peak_kind = measured_peak()
+    ach32 = BYTES_NN["f32"] * vh / (d32 * 1e-3) / 1e9
+    ach64 = BYTES_NN["f64"] * vh / (d64 * 1e-3) / 1e9
+    traffic = ncu_traffic("dslash_f32_nn_32^4")
+    roofline = {"bound": "hbm", "kernel": "dslash_kernel<float, one-hop> (D_oe, 32^4)", "achieved": round(ach32, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach32 / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} HBM copy bandwidth", "bytes_per_site": BYTES_NN["f32"],
+                "sites_per_launch": vh, "avg_launch_ms": round(d32, 5)}
+    dslash = {
+        "f32": {"ms": round(d32, 5), "GB/s": round(ach32, 1), "GFLOP/s": round(FLOP_NN * vh / (d32 * 1e-3) / 1e9, 1)},
+        "f64": {"ms": round(d64, 5), "GB/s": round(ach64, 1), "GFLOP/s": round(FLOP_NN * vh / (d64 * 1e-3) / 1e9, 1),
+                "bound": "fp64 alu (about 1.2 TFLOP/s of FP64 FMA on GB300)"},
+    }
+
+    # end to end from page-locked host buffers through qex_cg_host
+    e2e = None
+    if not args.no_e2e:
+        q.qex_cg_host(lat, "f32", U_h, None, 0.0, mass, B_h, X_h, tol=TOL, maxiter=200000, delta=DELTA)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            q.qex_cg_host(lat, "f32", U_h, None, 0.0, mass, B_h, X_h, tol=TOL, maxiter=200000, delta=DELTA)
+        torch.cuda.synchronize()
+        e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
+        e2e = {"value": round(dist.world / e2e_s, 4), "unit": "solves/s",
+               "h2d_bytes_per_step": U_h.numel() * 16 + B_h.numel() * 16, "d2h_bytes_per_step": X_h.numel() * 16,
+               "ms_per_step": round(e2e_s * 1e3, 3)}
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(wl, u, b, args.cpu_seconds, st64["iters"])
+        cpu["value"] = round(cpu["value"], 6)
+        cpu["seconds_per_solve"] = round(cpu["seconds_per_solve"], 2)
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_desc(wl), "lattice": list(dims), "mass": mass, "tol": TOL,
+                       "delta": DELTA, "parallelism": f"replicas{dist.world}",
+                       "l2": f"inputs larger than L2: {fat32.numel() * 4 / 1e6:.0f} MB FP32 and "
+                             f"{fat64.numel() * 8 / 1e6:.0f} MB FP64 links per step vs {L2_BYTES / 1e6:.0f} MB L2"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "mixed": {"iters": mixed["iters"], "reliable_updates": mixed["reliable_updates"],
+                      "true_rel_resid": mixed["true_rel_resid"], "solve_ms": round(mixed["time_ms"], 3)},
+            "fp64": {"iters": st64["iters"], "true_rel_resid": st64["true_rel_resid"],
+                     "solve_ms": round(st64["time_ms"], 3), "step_ms": round(fp64_ms, 3)},
+            "dslash": dslash,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    dist.close()
+
+
+# ------------------------------------------------------------------ reference
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if rank != 0:
+        return
+    import fieldgen as fg
+    import oracle
+
+    oracle.build()
+    wl = fg.workload(WORKLOAD)
+    u, b = make_inputs(wl)
+    iters = oracle_iterations(WORKLOAD)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle/workload_solves.json lacks the converged "
+                          "oracle iteration count for this workload"}))
+        return
+    t0 = time.perf_counter()
+    oracle.normal_op(wl["dims"], u, b, wl["mass"])
+    t_op = time.perf_counter() - t0
+    per_step = 90.0 / max(1, args.steps + args.warmup)
+    n = max(1, int(per_step / max(t_op, 1e-6)) - 2)
+    times = []
+    for k in range(args.warmup + args.steps):
+        s0 = time.perf_counter()
+        oracle.cg(wl["dims"], u, b, wl["mass"], tol=TOL, maxiter=n)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - s0)
+    t = sum(times) / len(times)
+    solve_s = t * (iters + 2) / (n + 2)
+    value = 1.0 / solve_s
+    sample = (f"oracle FP64 CG, {n} iterations per step on the full {'x'.join(map(str, wl['dims']))} lattice, "
+              f"scaled to the oracle's converged {iters} iterations + 2 residual evaluations")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(solve_s * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(wl).replace("mixed-precision", "FP64"), "lattice": list(wl["dims"]),
+                   "mass": wl["mass"], "tol": TOL, "parallelism": "host cores"},
+        "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(), "sample": sample, "value": round(value, 6)},
+        "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_dslash_only():
+    import torch
+
+    import fieldgen as fg
+    import paper_1612_02750_gb300 as q
+    from paper_1612_02750_gb300 import build as qbuild
+
+    qbuild.build()
+    wl = fg.workload(WORKLOAD)
+    u, b = make_inputs(wl)
+    lat = q.Lattice(wl["dims"], antiperiodic=True)
+    fat64 = q.qex_pack_links(lat, "f64", torch.from_numpy(u).cuda())
+    fat32 = q.qex_convert_links(lat, "f64", fat64, "f32")
+    src = torch.from_numpy(b).cuda()
+    for prec, fat in (("f32", fat32), ("f64", fat64)):
+        inp = q.qex_pack_field(lat, prec, 0, src)
+        for _ in range(2):
+            out = q.qex_dslash(lat, prec, fat, None, 0.0, 1, inp)
+    torch.cuda.synchronize()
+    print("dslash-only done", float(out.abs().sum()))
+
+
+def main():
+    args = parse()
+    if args.dslash_only:
+        run_dslash_only()
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -192,6 +192,24 @@ qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, con
                   void *x64, double tol, int maxiter, double delta, void *stream,
                   qex_cg_stats *stats);
 
+/* End-to-end solve from HOST memory (the call for users whose fields live
+ * on the host).  host_fat (and host_lng, or NULL) are canonical complex-double
+ * links [V][4][3][3]; host_b is a canonical complex-double field [V][3] whose
+ * even sites are the source.  The call copies them to the device, packs them
+ * (and rounds FP32 copies when inner = QEX_F32), solves exactly as qex_cg from
+ * x0 = 0, and writes the solution to the even sites of host_x (canonical
+ * [V][3]; its odd sites are set to zero).  Page-locked host buffers make the
+ * copies asynchronous DMA.  Device staging (canonical and internal copies) is
+ * owned by the lattice, allocated on first use and reused.  Synchronises the
+ * stream.  Errors as qex_cg. */
+qex_status qex_cg_host(const qex_lattice *lat, qex_prec inner, const double *host_fat, const double *host_lng,
+                       double c_naik, double mass, const double *host_b, double *host_x, double tol, int maxiter,
+                       double delta, void *stream, qex_cg_stats *stats);
+
+/* Number of kernels this library has launched in the calling process so far
+ * (monotone counter, for accounting of the kernels in a timed region). */
+uint64_t qex_launch_count(void);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *qex_last_error(void);
 

@@ -82,6 +82,8 @@ def load():
         "qex_norm2": (i, [vp, i, vp, vp, vp]),
         "qex_dot": (i, [vp, i, vp, vp, vp, vp]),
         "qex_cg": (i, [vp, i, vp, vp, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_cg_host": (i, [vp, i, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
     }
@@ -99,7 +101,7 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_last_error", "qex_version"]
+            "qex_cg_host", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -315,6 +317,35 @@ def qex_cg(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, mass:
     if check:
         _check(st)
     return st, stats.as_dict()
+
+
+def _host_ptr(t, dtype):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"host tensor must be contiguous {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def qex_cg_host(lat: Lattice, inner, host_fat, host_lng, c_naik: float, mass: float, host_b, host_x=None,
+                tol: float = 1e-10, maxiter: int = 100000, delta: float = 0.1, stream=None, check: bool = True):
+    """End-to-end solve from host tensors (canonical complex128 links and
+    fields; pinned memory for asynchronous copies).  Returns (host_x, status,
+    stats dict)."""
+    if host_x is None:
+        host_x = torch.empty_like(host_b)
+    stats = CgStats()
+    st = load().qex_cg_host(lat.handle, _prec(inner), _host_ptr(host_fat, torch.complex128),
+                            None if host_lng is None else _host_ptr(host_lng, torch.complex128), float(c_naik),
+                            float(mass), _host_ptr(host_b, torch.complex128), _host_ptr(host_x, torch.complex128),
+                            float(tol), int(maxiter), float(delta), _stream(stream), ctypes.byref(stats))
+    if check:
+        _check(st)
+    return host_x, st, stats.as_dict()
+
+
+def qex_launch_count() -> int:
+    return int(load().qex_launch_count())
 
 
 def qex_last_error() -> str:

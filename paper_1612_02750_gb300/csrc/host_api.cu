@@ -1,0 +1,87 @@
+// host_api.cu -- qex_cg_host: the whole path from host buffers (copy in,
+// pack, convert, solve, unpack, copy out) in one call.
+#include <string.h>
+
+#include "qex_kernels.cuh"
+
+using namespace qex;
+
+static size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
+
+extern "C" qex_status qex_cg_host(const qex_lattice *latc, qex_prec inner, const double *host_fat,
+                                  const double *host_lng, double c_naik, double mass, const double *host_b,
+                                  double *host_x, double tol, int maxiter, double delta, void *stream,
+                                  qex_cg_stats *stats) {
+    qex_status st;
+    if ((st = check_lattice(latc)) || (st = check_prec(inner))) return st;
+    if (!host_fat || !host_b || !host_x) {
+        set_error("host_fat, host_b and host_x must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    qex_lattice *lat = const_cast<qex_lattice *>(latc);
+    const bool naik = host_lng != nullptr;
+    const bool mixed = inner == QEX_F32;
+    const size_t lex_links = (size_t)lat->volume * 4 * 18 * sizeof(double);
+    const size_t lex_field = (size_t)lat->volume * 6 * sizeof(double);
+    const size_t l64 = qex_links_bytes(lat, QEX_F64), l32 = qex_links_bytes(lat, QEX_F32);
+    const size_t f64 = qex_field_bytes(lat, QEX_F64);
+    // staging: canonical links, canonical field, internal links (F64 [+F32]) x (fat [+long]), b, x
+    const int nsets = naik ? 2 : 1;
+    size_t need = al256(lex_links) + al256(lex_field) + nsets * (al256(l64) + (mixed ? al256(l32) : 0)) +
+                  2 * al256(f64);
+    if (lat->host_work_bytes < need) {
+        if (lat->host_work) {
+            QEX_CUDA(cudaDeviceSynchronize());
+            QEX_CUDA(cudaFree(lat->host_work));
+            lat->host_work = nullptr;
+            lat->host_work_bytes = 0;
+        }
+        QEX_CUDA(cudaMalloc(&lat->host_work, need));
+        lat->host_work_bytes = need;
+    }
+    char *w = (char *)lat->host_work;
+    double *d_lex = (double *)w;
+    w += al256(lex_links);
+    double *d_field = (double *)w;
+    w += al256(lex_field);
+    void *fat64 = w;
+    w += al256(l64);
+    void *fat32 = nullptr, *lng64 = nullptr, *lng32 = nullptr;
+    if (mixed) {
+        fat32 = w;
+        w += al256(l32);
+    }
+    if (naik) {
+        lng64 = w;
+        w += al256(l64);
+        if (mixed) {
+            lng32 = w;
+            w += al256(l32);
+        }
+    }
+    void *b64 = w;
+    w += al256(f64);
+    void *x64 = w;
+    cudaStream_t s = as_stream(stream);
+
+    QEX_CUDA(cudaMemcpyAsync(d_lex, host_fat, lex_links, cudaMemcpyHostToDevice, s));
+    if ((st = qex_pack_links(lat, QEX_F64, d_lex, fat64, stream))) return st;
+    if (mixed && (st = qex_convert_links(lat, QEX_F64, fat64, QEX_F32, fat32, stream))) return st;
+    if (naik) {
+        QEX_CUDA(cudaMemcpyAsync(d_lex, host_lng, lex_links, cudaMemcpyHostToDevice, s));
+        if ((st = qex_pack_links(lat, QEX_F64, d_lex, lng64, stream))) return st;
+        if (mixed && (st = qex_convert_links(lat, QEX_F64, lng64, QEX_F32, lng32, stream))) return st;
+    }
+    QEX_CUDA(cudaMemcpyAsync(d_field, host_b, lex_field, cudaMemcpyHostToDevice, s));
+    if ((st = qex_pack_field(lat, QEX_F64, 0, d_field, b64, stream))) return st;
+    QEX_CUDA(cudaMemsetAsync(x64, 0, f64, s));
+    qex_status solve = qex_cg(lat, inner, fat64, lng64, fat32, lng32, c_naik, mass, b64, x64, tol, maxiter, delta,
+                              stream, stats);
+    if (solve != QEX_OK && solve != QEX_ERR_NOT_CONVERGED) return solve;
+    QEX_CUDA(cudaMemsetAsync(d_field, 0, lex_field, s));
+    if ((st = qex_unpack_field(lat, QEX_F64, 0, x64, d_field, stream))) return st;
+    QEX_CUDA(cudaMemcpyAsync(host_x, d_field, lex_field, cudaMemcpyDeviceToHost, s));
+    QEX_CUDA(cudaStreamSynchronize(s));
+    if (solve != QEX_OK) set_error("CG did not converge in %d iterations", maxiter);
+    return solve;
+}

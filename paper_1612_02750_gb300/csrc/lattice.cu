@@ -4,11 +4,16 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "qex_kernels.cuh"
 
 namespace qex {
 
 static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches(0);
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -133,6 +138,8 @@ const char *qex_last_error(void) { return g_err; }
 
 const char *qex_version(void) { return "qex_gpu 0.1 (sm_103a)"; }
 
+uint64_t qex_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
 qex_status qex_lattice_create(const int dims[4], int antiperiodic_t, qex_lattice **out) {
     if (!dims || !out) {
         set_error("dims and out must not be NULL");
@@ -177,6 +184,7 @@ qex_status qex_lattice_destroy(qex_lattice *lat) {
     if (lat->scalars_host) cudaFreeHost(lat->scalars_host);
     if (lat->scalars_host2) cudaFreeHost(lat->scalars_host2);
     if (lat->work) cudaFree(lat->work);
+    if (lat->host_work) cudaFree(lat->host_work);
     if (lat->ev0) cudaEventDestroy(lat->ev0);
     if (lat->ev1) cudaEventDestroy(lat->ev1);
     delete lat;

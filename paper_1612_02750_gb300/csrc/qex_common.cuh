@@ -25,10 +25,13 @@ qex_status cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::qex::cuda_fail(_e, #call);  \
     } while (0)
 
+void note_launch();
+
 #define QEX_CHECK_LAUNCH(what)                                      \
     do {                                                            \
         cudaError_t _e = cudaGetLastError();                        \
         if (_e != cudaSuccess) return ::qex::cuda_fail(_e, what);   \
+        ::qex::note_launch();                                       \
     } while (0)
 
 // ------------------------------------------------------- fast division
@@ -299,6 +302,8 @@ struct qex_lattice {
     qex::CgScalars *scalars_host2;  // pinned readback slot 1
     void *work;                // CG work vectors
     size_t work_bytes;
+    void *host_work;           // staging of qex_cg_host
+    size_t host_work_bytes;
     cudaEvent_t ev0, ev1;
 };
 
