@@ -161,6 +161,36 @@ qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat,
                          double c_naik, double mass, const void *in, void *out, void *tmp_odd,
                          void *stream);
 
+/* Size of the static device scratch behind qex_normal_op_static (32 MiB). */
+#define QEX_NORMAL_OP_STATIC_MAX_BYTES ((size_t)32 << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory.  qex_normal_op needs a caller-allocated
+ * odd half field (tmp_odd) for D_oe in; callers running under an allocator
+ * that forbids allocations outside its own pool, or on paths where the
+ * device-wide synchronisation of cudaMalloc/cudaFree is not acceptable, may
+ * have no way to provide one.  This variant computes the same
+ * out = (m^2 - D_eo D_oe) in, but keeps D_oe in in a fixed array compiled
+ * into the library (a file-scope __device__ array of
+ * QEX_NORMAL_OP_STATIC_MAX_BYTES bytes), so it allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine.  The caller still
+ * passes the links, `in` and `out` (device memory, as for qex_normal_op).
+ * - Size limit: the intermediate half field, qex_field_bytes(lat, prec),
+ *   must fit in QEX_NORMAL_OP_STATIC_MAX_BYTES (FP64: Vh <= 699,050 sites,
+ *   e.g. 32^4; FP32: Vh <= 1,398,101 sites); larger lattices get
+ *   QEX_ERR_SHAPE before anything is launched.
+ * - Memory: every GPU that loads the library holds the array until the
+ *   process exits.
+ * - Set-up: the first call made with a given device current looks up the
+ *   array's device address (cudaGetSymbolAddress) for that device; make that
+ *   first call before any stream capture.
+ * - Sharing: every call on every lattice uses the same array, and it keeps
+ *   the last call's contents (each call overwrites what it reads).  Calls
+ *   whose kernels overlap on the GPU (different streams, or host threads
+ *   without ordering) race on the array: order them on one stream. */
+qex_status qex_normal_op_static(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
+                                double c_naik, double mass, const void *in, void *out, void *stream);
+
 /* ||f||^2 of a half field, accumulated in FP64 in a fixed order
  * (bit-reproducible run to run); written to dev_out (one double, device). */
 qex_status qex_norm2(const qex_lattice *lat, qex_prec prec, const void *f, double *dev_out,

@@ -292,6 +292,20 @@ def qex_normal_op(lat: Lattice, prec, fat, lng, c_naik: float, mass: float, inp,
     return out
 
 
+def qex_normal_op_static(lat: Lattice, prec, fat, lng, c_naik: float, mass: float, inp, out=None, stream=None):
+    """(m^2 - D_eo D_oe) inp with the intermediate in the library's static
+    device scratch (no allocation inside the call; ``out`` is allocated here
+    only when not given)."""
+    fn = load().qex_normal_op_static
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    out = empty_field(lat, prec) if out is None else out
+    _check(fn(lat.handle, _prec(prec), _ptr(fat), _ptr(lng), float(c_naik), float(mass), _ptr(inp), _ptr(out),
+              _stream(stream)))
+    return out
+
+
 def qex_norm2(lat: Lattice, prec, f, out=None, stream=None):
     out = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
     _check(load().qex_norm2(lat.handle, _prec(prec), _ptr(f), _ptr(out), _stream(stream)))
