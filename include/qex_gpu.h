@@ -32,11 +32,12 @@
  *     links: per parity p, per direction mu, structure-of-arrays planes over
  *            the Vh sites of parity p.  F64: 9 planes of double2 (matrix
  *            element c = 3a+b); F32: 4 planes of float4 (elements 0-1, 2-3,
- *            4-5, 6-7) and 1 plane of float2 (element 8).  Size
+ *            4-5, 6-7) and 1 plane of float2 (element 8); F32_R12: 3 planes
+ *            of float4 (elements 0-1, 2-3, 4-5: rows 0 and 1).  Size
  *            qex_links_bytes().
  *     half field (the Vh sites of one parity): F64: 3 planes of double2
- *            (colour a); F32: 1 plane of float4 (colours 0,1) + 1 plane of
- *            float2 (colour 2).  Size qex_field_bytes().
+ *            (colour a); F32 and F32_R12: 1 plane of float4 (colours 0,1) +
+ *            1 plane of float2 (colour 2).  Size qex_field_bytes().
  * - All field and link pointers are caller-owned DEVICE memory, 16-byte
  *   aligned; the library never frees them.  The library owns only the
  *   lattice object and its scratch (created lazily, freed by destroy).
@@ -70,7 +71,13 @@ typedef enum {
     QEX_ERR_NAN = 7              /* NaN/Inf met in a reduction, or CG breakdown */
 } qex_status;
 
-typedef enum { QEX_F64 = 0, QEX_F32 = 1 } qex_prec;
+/* Precisions.  QEX_F32_R12 means FP32 fields and FP32 fat links stored as
+ * their first two rows only (12 reals); the third row is rebuilt in the
+ * kernel as the complex conjugate of the cross product of the first two,
+ * which is exact for SU(3) matrices only -- use it for unitary, unimodular
+ * links.  Long (Naik) links are never compressed: with QEX_F32_R12 the long
+ * link set is in QEX_F32 format. */
+typedef enum { QEX_F64 = 0, QEX_F32 = 1, QEX_F32_R12 = 2 } qex_prec;
 
 typedef struct qex_lattice qex_lattice; /* opaque, owned by the library */
 
@@ -207,8 +214,9 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  * ||b - A x|| / ||b|| <= tol, computed in FP64.
  *
  * inner = QEX_F64: plain CG in FP64 on fat64/lng64.
- * inner = QEX_F32: mixed precision: the CG iteration runs in FP32 on
- *   fat32/lng32 (inner residual and iterate in FP32, all reductions in FP64);
+ * inner = QEX_F32 or QEX_F32_R12: mixed precision: the CG iteration runs in
+ *   FP32 on fat32/lng32 (fat32 in the `inner` link format, lng32 in QEX_F32;
+ *   inner residual and iterate in FP32, all reductions in FP64);
  *   whenever the iterated residual norm drops below delta times its maximum
  *   since the last update (or meets tol), the FP64 solution is updated and the
  *   residual is recomputed in FP64 with fat64/lng64 (reliable update).
@@ -226,7 +234,7 @@ qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, con
  * on the host).  host_fat (and host_lng, or NULL) are canonical complex-double
  * links [V][4][3][3]; host_b is a canonical complex-double field [V][3] whose
  * even sites are the source.  The call copies them to the device, packs them
- * (and rounds FP32 copies when inner = QEX_F32), solves exactly as qex_cg from
+ * (and rounds FP32 copies when inner is QEX_F32 or QEX_F32_R12), solves as qex_cg from
  * x0 = 0, and writes the solution to the even sites of host_x (canonical
  * [V][3]; its odd sites are set to zero).  Page-locked host buffers make the
  * copies asynchronous DMA.  Device staging (canonical and internal copies) is

@@ -64,6 +64,7 @@ static qex_status carve(qex_lattice *lat, bool mixed, CgBuffers &B) {
 struct Solve {
     qex_lattice *lat;
     bool mixed;
+    qex_prec inner;
     const void *fat64, *lng64, *fat32, *lng32;
     double c3, m2;
     const double *b64;
@@ -77,7 +78,7 @@ static qex_status enqueue_iteration(Solve &s) {
     qex_lattice *lat = s.lat;
     CgScalars *S = lat->scalars;
     DslashArgs a = {};
-    a.prec = s.mixed ? QEX_F32 : QEX_F64;
+    a.prec = s.inner;
     a.fat = s.mixed ? s.fat32 : s.fat64;
     a.lng = s.mixed ? s.lng32 : s.lng64;
     a.c3 = s.c3;
@@ -157,7 +158,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
                              qex_cg_stats *stats) {
     qex_status st;
     if ((st = check_lattice(latc)) || (st = check_prec(inner))) return st;
-    const bool mixed = inner == QEX_F32;
+    const bool mixed = inner != QEX_F64;
     if ((st = check_dslash_args(latc, QEX_F64, fat64, lng64, b64, x64))) return st;
     if (mixed) {
         if (!fat32 || !aligned16(fat32) || (lng64 && (!lng32 || !aligned16(lng32)))) {
@@ -177,6 +178,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     Solve s;
     s.lat = lat;
     s.mixed = mixed;
+    s.inner = inner;
     s.fat64 = fat64;
     s.lng64 = lng64;
     s.fat32 = fat32;

@@ -8,11 +8,23 @@
 // for the long links and the x +- 3mu neighbours.  Staggered phases and the
 // antiperiodic time boundary are computed from the site coordinates; no phase
 // is folded into the links.
+#include <type_traits>
+
 #include "qex_kernels.cuh"
 
 namespace qex {
 
-template <typename R, bool NAIK, int EPI>
+// Fat-link formats: 0 = full 3x3 in the field precision, 1 = FP32 two-row
+// (third row rebuilt in registers).
+template <typename R, int FMT>
+__device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int mu, int i) {
+    if constexpr (FMT == 1)
+        return load_link_r12(base, vh, p, mu, i);
+    else
+        return load_link(base, vh, p, mu, i);
+}
+
+template <typename R, int FMT, bool NAIK, int EPI>
 __global__ void __launch_bounds__(kBlock)
 dslash_kernel(Geom g, const R *__restrict__ fat, const R *__restrict__ lng, R c3, int p,
               const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ q,
@@ -35,13 +47,13 @@ dslash_kernel(Geom g, const R *__restrict__ fat, const R *__restrict__ lng, R c3
             const R eta = eta_bit(s, mu) ? R(-1) : R(1);
             {   // + eta b U_mu(x) psi(x + mu)
                 const int j = hop_index(g, s, mu, 1);
-                const Mat3<R> u = load_link(fat, vh, p, mu, i);
+                const Mat3<R> u = load_fat<R, FMT>(fat, vh, p, mu, i);
                 const Vec3<R> v = load_vec(in, vh, j);
                 acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, v);
             }
             {   // - eta b U_mu(x - mu)^+ psi(x - mu)
                 const int j = hop_index(g, s, mu, -1);
-                const Mat3<R> u = load_link(fat, vh, 1 - p, mu, j);
+                const Mat3<R> u = load_fat<R, FMT>(fat, vh, 1 - p, mu, j);
                 const Vec3<R> v = load_vec(in, vh, j);
                 acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, v);
             }
@@ -137,22 +149,22 @@ dslash_kernel(Geom g, const R *__restrict__ fat, const R *__restrict__ lng, R c3
     }
 }
 
-template <typename R, bool NAIK, int EPI>
+template <typename R, int FMT, bool NAIK, int EPI>
 static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     int nb = blocks_for(lat->vh);
-    dslash_kernel<R, NAIK, EPI><<<nb, kBlock, 0, st>>>(
+    dslash_kernel<R, FMT, NAIK, EPI><<<nb, kBlock, 0, st>>>(
         lat->geom, (const R *)a.fat, (const R *)a.lng, (R)a.c3, a.out_parity, (const R *)a.in, (R *)a.out,
         (const R *)a.q, a.b, (R)a.m2, a.S, a.check_halt, lat->partials, lat->counter);
 }
 
-template <typename R, bool NAIK>
+template <typename R, int FMT, bool NAIK>
 static void launch_epi(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     if (a.epi == EPI_PLAIN)
-        launch_t<R, NAIK, EPI_PLAIN>(lat, a, st);
+        launch_t<R, FMT, NAIK, EPI_PLAIN>(lat, a, st);
     else if (a.epi == EPI_NORMAL)
-        launch_t<R, NAIK, EPI_NORMAL>(lat, a, st);
-    else
-        launch_t<R, NAIK, EPI_RESID>(lat, a, st);
+        launch_t<R, FMT, NAIK, EPI_NORMAL>(lat, a, st);
+    else if constexpr (std::is_same<R, double>::value)
+        launch_t<R, FMT, NAIK, EPI_RESID>(lat, a, st);
 }
 
 qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
@@ -162,18 +174,25 @@ qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st)
     }
     if (a.prec == QEX_F64) {
         if (a.lng)
-            launch_epi<double, true>(lat, a, st);
+            launch_epi<double, 0, true>(lat, a, st);
         else
-            launch_epi<double, false>(lat, a, st);
+            launch_epi<double, 0, false>(lat, a, st);
     } else {
         if (a.epi == EPI_RESID) {
             set_error("the residual epilogue is FP64 only");
             return QEX_ERR_ARG;
         }
-        if (a.lng)
-            launch_epi<float, true>(lat, a, st);
-        else
-            launch_epi<float, false>(lat, a, st);
+        if (a.prec == QEX_F32_R12) {
+            if (a.lng)
+                launch_epi<float, 1, true>(lat, a, st);
+            else
+                launch_epi<float, 1, false>(lat, a, st);
+        } else {
+            if (a.lng)
+                launch_epi<float, 0, true>(lat, a, st);
+            else
+                launch_epi<float, 0, false>(lat, a, st);
+        }
     }
     QEX_CHECK_LAUNCH("dslash_kernel");
     return QEX_OK;

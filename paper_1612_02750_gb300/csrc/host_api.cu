@@ -20,10 +20,10 @@ extern "C" qex_status qex_cg_host(const qex_lattice *latc, qex_prec inner, const
     }
     qex_lattice *lat = const_cast<qex_lattice *>(latc);
     const bool naik = host_lng != nullptr;
-    const bool mixed = inner == QEX_F32;
+    const bool mixed = inner != QEX_F64;
     const size_t lex_links = (size_t)lat->volume * 4 * 18 * sizeof(double);
     const size_t lex_field = (size_t)lat->volume * 6 * sizeof(double);
-    const size_t l64 = qex_links_bytes(lat, QEX_F64), l32 = qex_links_bytes(lat, QEX_F32);
+    const size_t l64 = qex_links_bytes(lat, QEX_F64), l32 = qex_links_bytes(lat, QEX_F32);  // >= R12 size
     const size_t f64 = qex_field_bytes(lat, QEX_F64);
     // staging: canonical links, canonical field, internal links (F64 [+F32]) x (fat [+long]), b, x
     const int nsets = naik ? 2 : 1;
@@ -66,7 +66,7 @@ extern "C" qex_status qex_cg_host(const qex_lattice *latc, qex_prec inner, const
 
     QEX_CUDA(cudaMemcpyAsync(d_lex, host_fat, lex_links, cudaMemcpyHostToDevice, s));
     if ((st = qex_pack_links(lat, QEX_F64, d_lex, fat64, stream))) return st;
-    if (mixed && (st = qex_convert_links(lat, QEX_F64, fat64, QEX_F32, fat32, stream))) return st;
+    if (mixed && (st = qex_convert_links(lat, QEX_F64, fat64, inner, fat32, stream))) return st;
     if (naik) {
         QEX_CUDA(cudaMemcpyAsync(d_lex, host_lng, lex_links, cudaMemcpyHostToDevice, s));
         if ((st = qex_pack_links(lat, QEX_F64, d_lex, lng64, stream))) return st;

@@ -46,6 +46,41 @@ __device__ __forceinline__ void get_link(const float *base, size_t vh, int blk, 
     m[17] = v.y;
 }
 
+// Two-row FP32 links: rows 0 and 1 (elements 0..5) in 3 float4 planes.
+struct R12 {
+    float *p;
+};
+struct R12c {
+    const float *p;
+};
+
+__device__ __forceinline__ void put_link(R12 base, size_t vh, int blk, int i, const double *m) {
+    float4 *b4 = reinterpret_cast<float4 *>(base.p + (size_t)blk * 12 * vh) + i;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        b4[q * vh] = make_float4((float)m[4 * q], (float)m[4 * q + 1], (float)m[4 * q + 2], (float)m[4 * q + 3]);
+}
+
+// Reads the two stored rows and rebuilds the third in FP64.
+__device__ __forceinline__ void get_link(R12c base, size_t vh, int blk, int i, double *m) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(base.p + (size_t)blk * 12 * vh) + i;
+    Mat3<double> u;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float4 v = b4[q * vh];
+        u.e[2 * q].re = v.x;
+        u.e[2 * q].im = v.y;
+        u.e[2 * q + 1].re = v.z;
+        u.e[2 * q + 1].im = v.w;
+    }
+    reconstruct_row2(u);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        m[2 * c] = u.e[c].re;
+        m[2 * c + 1] = u.e[c].im;
+    }
+}
+
 __device__ __forceinline__ void put_vec(double *base, size_t vh, int i, const double *v) {
     double2 *b = reinterpret_cast<double2 *>(base) + i;
 #pragma unroll
@@ -80,7 +115,7 @@ __device__ __forceinline__ void get_vec(const float *base, size_t vh, int i, dou
 
 // blockIdx.y = p*4 + mu; one thread per site of parity p.
 template <typename R>
-__global__ void pack_links_kernel(Geom g, const double *__restrict__ lex, R *__restrict__ out) {
+__global__ void pack_links_kernel(Geom g, const double *__restrict__ lex, R out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.vh) return;
     int blk = blockIdx.y, p = blk >> 2, mu = blk & 3;
@@ -93,7 +128,7 @@ __global__ void pack_links_kernel(Geom g, const double *__restrict__ lex, R *__r
 }
 
 template <typename R>
-__global__ void unpack_links_kernel(Geom g, const R *__restrict__ in, double *__restrict__ lex) {
+__global__ void unpack_links_kernel(Geom g, R in, double *__restrict__ lex) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.vh) return;
     int blk = blockIdx.y, p = blk >> 2, mu = blk & 3;
@@ -106,7 +141,7 @@ __global__ void unpack_links_kernel(Geom g, const R *__restrict__ in, double *__
 }
 
 template <typename RI, typename RO>
-__global__ void convert_links_kernel(int vh, const RI *__restrict__ in, RO *__restrict__ out) {
+__global__ void convert_links_kernel(int vh, RI in, RO out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= vh) return;
     double m[18];
@@ -159,6 +194,16 @@ static qex_status check_ptrs(const void *a, const void *b) {
     return QEX_OK;
 }
 
+template <typename RI>
+static void convert_links_to(qex_prec to, int vh, RI in, void *out, dim3 grid, cudaStream_t s) {
+    if (to == QEX_F64)
+        convert_links_kernel<RI, double *><<<grid, kBlock, 0, s>>>(vh, in, (double *)out);
+    else if (to == QEX_F32)
+        convert_links_kernel<RI, float *><<<grid, kBlock, 0, s>>>(vh, in, (float *)out);
+    else
+        convert_links_kernel<RI, R12><<<grid, kBlock, 0, s>>>(vh, in, R12{(float *)out});
+}
+
 }  // namespace qex
 
 using namespace qex;
@@ -170,10 +215,13 @@ qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *l
     qex_status st;
     if ((st = check_lattice(lat)) || (st = check_prec(prec)) || (st = check_ptrs(lex_links, internal))) return st;
     dim3 grid(blocks_for(lat->vh), 8);
+    cudaStream_t s = as_stream(stream);
     if (prec == QEX_F64)
-        pack_links_kernel<double><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, lex_links, (double *)internal);
+        pack_links_kernel<double *><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, (double *)internal);
+    else if (prec == QEX_F32)
+        pack_links_kernel<float *><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, (float *)internal);
     else
-        pack_links_kernel<float><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, lex_links, (float *)internal);
+        pack_links_kernel<R12><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, R12{(float *)internal});
     QEX_CHECK_LAUNCH("pack_links_kernel");
     return QEX_OK;
 }
@@ -183,10 +231,13 @@ qex_status qex_unpack_links(const qex_lattice *lat, qex_prec prec, const void *i
     qex_status st;
     if ((st = check_lattice(lat)) || (st = check_prec(prec)) || (st = check_ptrs(lex_links, internal))) return st;
     dim3 grid(blocks_for(lat->vh), 8);
+    cudaStream_t s = as_stream(stream);
     if (prec == QEX_F64)
-        unpack_links_kernel<double><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, (const double *)internal, lex_links);
+        unpack_links_kernel<const double *><<<grid, kBlock, 0, s>>>(lat->geom, (const double *)internal, lex_links);
+    else if (prec == QEX_F32)
+        unpack_links_kernel<const float *><<<grid, kBlock, 0, s>>>(lat->geom, (const float *)internal, lex_links);
     else
-        unpack_links_kernel<float><<<grid, kBlock, 0, as_stream(stream)>>>(lat->geom, (const float *)internal, lex_links);
+        unpack_links_kernel<R12c><<<grid, kBlock, 0, s>>>(lat->geom, R12c{(const float *)internal}, lex_links);
     QEX_CHECK_LAUNCH("unpack_links_kernel");
     return QEX_OK;
 }
@@ -200,7 +251,7 @@ qex_status qex_pack_field(const qex_lattice *lat, qex_prec prec, int parity, con
         return QEX_ERR_ARG;
     }
     int nb = blocks_for(lat->vh);
-    if (prec == QEX_F64)
+    if (is_f64(prec))
         pack_field_kernel<double><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, lex_field, (double *)half);
     else
         pack_field_kernel<float><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, lex_field, (float *)half);
@@ -217,7 +268,7 @@ qex_status qex_unpack_field(const qex_lattice *lat, qex_prec prec, int parity, c
         return QEX_ERR_ARG;
     }
     int nb = blocks_for(lat->vh);
-    if (prec == QEX_F64)
+    if (is_f64(prec))
         unpack_field_kernel<double><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const double *)half, lex_field);
     else
         unpack_field_kernel<float><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const float *)half, lex_field);
@@ -233,14 +284,12 @@ qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *
     dim3 grid(blocks_for(lat->vh), 8);
     cudaStream_t s = as_stream(stream);
     int vh = (int)lat->vh;
-    if (from == QEX_F64 && to == QEX_F32)
-        convert_links_kernel<double, float><<<grid, kBlock, 0, s>>>(vh, (const double *)in, (float *)out);
-    else if (from == QEX_F32 && to == QEX_F64)
-        convert_links_kernel<float, double><<<grid, kBlock, 0, s>>>(vh, (const float *)in, (double *)out);
-    else if (from == QEX_F64)
-        convert_links_kernel<double, double><<<grid, kBlock, 0, s>>>(vh, (const double *)in, (double *)out);
+    if (from == QEX_F64)
+        convert_links_to<const double *>(to, vh, (const double *)in, out, grid, s);
+    else if (from == QEX_F32)
+        convert_links_to<const float *>(to, vh, (const float *)in, out, grid, s);
     else
-        convert_links_kernel<float, float><<<grid, kBlock, 0, s>>>(vh, (const float *)in, (float *)out);
+        convert_links_to<R12c>(to, vh, R12c{(const float *)in}, out, grid, s);
     QEX_CHECK_LAUNCH("convert_links_kernel");
     return QEX_OK;
 }
@@ -253,11 +302,11 @@ qex_status qex_convert_field(const qex_lattice *lat, qex_prec from, const void *
     int nb = blocks_for(lat->vh);
     cudaStream_t s = as_stream(stream);
     int vh = (int)lat->vh;
-    if (from == QEX_F64 && to == QEX_F32)
+    if (is_f64(from) && !is_f64(to))
         convert_field_kernel<double, float><<<nb, kBlock, 0, s>>>(vh, (const double *)in, (float *)out);
-    else if (from == QEX_F32 && to == QEX_F64)
+    else if (!is_f64(from) && is_f64(to))
         convert_field_kernel<float, double><<<nb, kBlock, 0, s>>>(vh, (const float *)in, (double *)out);
-    else if (from == QEX_F64)
+    else if (is_f64(from))
         convert_field_kernel<double, double><<<nb, kBlock, 0, s>>>(vh, (const double *)in, (double *)out);
     else
         convert_field_kernel<float, float><<<nb, kBlock, 0, s>>>(vh, (const float *)in, (float *)out);

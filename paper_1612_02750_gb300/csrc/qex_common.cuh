@@ -173,6 +173,39 @@ __device__ __forceinline__ Mat3<float> load_link(const float *base, size_t vh, i
     return m;
 }
 
+// Third row of an SU(3) matrix from its first two: row2 = conj(row0 x row1).
+template <typename R>
+__host__ __device__ __forceinline__ void reconstruct_row2(Mat3<R> &m) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        const Cplx<R> a = m.e[k], b = m.e[3 + l], c = m.e[l], d = m.e[3 + k];
+        R re = a.re * b.re - a.im * b.im;
+        R im = a.re * b.im + a.im * b.re;
+        re -= c.re * d.re - c.im * d.im;
+        im -= c.re * d.im + c.im * d.re;
+        m.e[6 + j].re = re;
+        m.e[6 + j].im = -im;
+    }
+}
+
+// Two-row FP32 link: block (p, mu) holds 3 float4 planes {e0,e1}, {e2,e3},
+// {e4,e5}; block size 12*Vh floats.
+__device__ __forceinline__ Mat3<float> load_link_r12(const float *base, size_t vh, int p, int mu, int i) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(base + (size_t)(p * 4 + mu) * 12 * vh) + i;
+    Mat3<float> m;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float4 v = __ldg(b4 + q * vh);
+        m.e[2 * q].re = v.x;
+        m.e[2 * q].im = v.y;
+        m.e[2 * q + 1].re = v.z;
+        m.e[2 * q + 1].im = v.w;
+    }
+    reconstruct_row2(m);
+    return m;
+}
+
 __device__ __forceinline__ Vec3<double> load_vec(const double *base, size_t vh, int i) {
     const double2 *b = reinterpret_cast<const double2 *>(base) + i;
     Vec3<double> v;
@@ -315,6 +348,7 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 qex_status check_lattice(const qex_lattice *lat);
 qex_status check_prec(qex_prec prec);
+inline bool is_f64(qex_prec p) { return p == QEX_F64; }
 
 constexpr int kBlock = 256;  // threads per block of the site kernels
 

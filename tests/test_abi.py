@@ -114,4 +114,7 @@ def test_argument_errors(lib):
     assert lib.qex_eo_index(h, (ctypes.c_int * 4)(0, 0, 2, 0)) == -1
     assert lib.qex_links_bytes(h, 0) == 4 * 128 * 18 * 8
     assert lib.qex_field_bytes(h, 1) == 64 * 6 * 4
+    assert lib.qex_links_bytes(h, 2) == 4 * 128 * 12 * 4
+    assert lib.qex_field_bytes(h, 2) == 64 * 6 * 4
+    assert lib.qex_pack_links(h, 3, None, None, None) == 1  # unknown precision
     lib.qex_lattice_destroy(h)

@@ -14,7 +14,7 @@ import fieldgen as fg
 pytestmark = pytest.mark.gpu
 
 C3 = -1.0 / 24.0
-TOL = {"f64": 1e-13, "f32": 1e-5}
+TOL = {"f64": 1e-13, "f32": 1e-5, "f32r12": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -59,10 +59,13 @@ class Setup:
         self.lat = q.Lattice(dims, antiperiodic)
         self.fat = {"f64": q.qex_pack_links(self.lat, "f64", dev(self.u))}
         self.fat["f32"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32")
-        self.lng = {"f64": None, "f32": None}
+        if fat in ("haar", "exp", "unit"):  # SU(3) links: two-row storage applies
+            self.fat["f32r12"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32r12")
+        self.lng = {"f64": None, "f32": None, "f32r12": None}
         if naik:
             self.lng["f64"] = q.qex_pack_links(self.lat, "f64", dev(self.w))
             self.lng["f32"] = q.qex_pack_links(self.lat, "f32", dev(self.w))
+            self.lng["f32r12"] = self.lng["f32"]  # long links are never compressed
 
     def half(self, prec, parity, field):
         return self.q.qex_pack_field(self.lat, prec, parity, dev(field))
@@ -107,9 +110,25 @@ def test_pack_roundtrip_bit_exact(q, dims):
     assert np.array_equal(host(q.qex_unpack_links(lat, "f64", l64)), u.astype(np.complex64).astype(np.complex128))
 
 
+@pytest.mark.parametrize("kind", ["haar", "exp"])
+def test_two_row_links_roundtrip(q, kind):
+    """SU(3) links stored as two FP32 rows come back with the third row rebuilt
+    to FP32 accuracy; pack and convert from FP64 give the same bits."""
+    dims = (6, 4, 4, 10)
+    u = fg.random_links(dims, kind, fg.rng_streams(9)["links"])
+    lat = q.Lattice(dims)
+    r12 = q.qex_pack_links(lat, "f32r12", dev(u))
+    assert r12.numel() * 4 == q.qex_links_bytes(lat, "f32r12") == int(np.prod(dims)) * 4 * 12 * 4
+    back = host(q.qex_unpack_links(lat, "f32r12", r12))
+    assert np.abs(back - u).max() <= 2e-6
+    assert np.array_equal(back[..., :2, :], u[..., :2, :].astype(np.complex64).astype(np.complex128))
+    via = q.qex_convert_links(lat, "f64", q.qex_pack_links(lat, "f64", dev(u)), "f32r12")
+    assert np.array_equal(host(via), host(r12))
+
+
 @pytest.mark.parametrize("dims", SHAPES)
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12"])
 def test_dslash_parity(q, oracle_mod, dims, naik, prec):
     S = Setup(q, dims, naik, seed=21)
     for ap in (True, False):
@@ -135,7 +154,7 @@ def test_dslash_exp_links_and_unit_links(q, oracle_mod):
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12"])
 def test_normal_op_parity(q, oracle_mod, naik, prec):
     dims = (8, 4, 6, 10)
     S = Setup(q, dims, naik, seed=22)
@@ -173,13 +192,14 @@ def _cg(q, S, inner, m, b_full, tol=1e-10, maxiter=20000, delta=0.1, x0=None):
 
     b = S.half("f64", 0, b_full)
     x = S.half("f64", 0, x0) if x0 is not None else torch.zeros_like(b)
-    st, stats = q.qex_cg(S.lat, inner, S.fat["f64"], S.lng["f64"], S.fat["f32"], S.lng["f32"], C3, m, b, x,
+    f32 = "f32r12" if inner == "f32r12" else "f32"
+    st, stats = q.qex_cg(S.lat, inner, S.fat["f64"], S.lng["f64"], S.fat[f32], S.lng["f32"], C3, m, b, x,
                          tol=tol, maxiter=maxiter, delta=delta, check=False)
     return st, stats, S.full("f64", 0, x)
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("inner", ["f64", "f32"])
+@pytest.mark.parametrize("inner", ["f64", "f32", "f32r12"])
 def test_cg_parity(q, oracle_mod, naik, inner):
     dims = (8, 8, 4, 8)
     m = 0.1
@@ -194,7 +214,7 @@ def test_cg_parity(q, oracle_mod, naik, inner):
     assert ok
     ev = fg.even_mask(dims)
     assert relerr(x[ev], xr[ev]) <= 1e-7
-    if inner == "f32":
+    if inner != "f64":
         assert stats["reliable_updates"] >= 1
 
 
