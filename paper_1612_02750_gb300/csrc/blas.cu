@@ -43,14 +43,32 @@ __device__ __forceinline__ R norm2_site(const Vec3<R> &v) {
     return s;
 }
 
-// x += alpha p; r -= alpha ap; ||r||^2 -> rr_new; then the CG scalar logic.
+__device__ __forceinline__ void set_conditions(const GraphCtl &ctl, unsigned int loop, unsigned int ru) {
+    if (ctl.active) {
+        cudaGraphSetConditional(ctl.loop, loop);
+        cudaGraphSetConditional(ctl.ru, ru);
+    }
+}
+
+// x += alpha p_new; r -= alpha ap; ||r||^2 -> rr_new; then the CG scalar
+// logic: continue (beta = rr_new / rr), or ask for a reliable update
+// (iterated residual small enough, or the iteration cap reached), or stop
+// on a NaN.  In the graph solve the last block also sets the loop and
+// reliable-update conditions; a halted entry clears both.
 template <typename R>
 __global__ void __launch_bounds__(kBlock)
-update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, const R *__restrict__ p,
-                 const R *__restrict__ ap, CgScalars *S, double *partials, unsigned int *counter) {
+update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf1, const R *__restrict__ ap,
+                 CgScalars *S, double *partials, unsigned int *counter, const GraphCtl ctl) {
     __shared__ double smem[32];
-    if (S->halt) return;
+    if (S->halt) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_conditions(ctl, 0u, 0u);
+        return;
+    }
+    // fail-safe: stop unless the last block (which runs after this block's
+    // fenced atomicAdd below) sets the conditions again
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_conditions(ctl, 0u, 0u);
     const R alpha = (R)S->alpha;
+    const R *p = (S->iters & 1) ? pbuf0 : pbuf1;  // the new direction
     double part = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
         Vec3<R> xv = load_vec(x, vh, i), rv = load_vec(r, vh, i);
@@ -69,9 +87,11 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, const R *__restri
     double rr_new;
     if (!grid_sum(part, partials, counter, smem, &rr_new)) return;
     S->iters += 1;
+    S->trips += 1;
     if (!isfinite(rr_new)) {
         S->error = 1;
         S->halt = 1;
+        set_conditions(ctl, 0u, 0u);
         return;
     }
     if (rr_new > S->rmax2) S->rmax2 = rr_new;
@@ -80,28 +100,12 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, const R *__restri
         // keeps the previous value so that beta is formed from the true one
         S->need_ru = 1;
         S->halt = 1;
+        set_conditions(ctl, S->trips < S->maxiter + 4 ? 1u : 0u, 1u);
         return;
     }
     S->beta = rr_new / S->rr;
     S->rr = rr_new;
-}
-
-// p = r + beta p
-template <typename R>
-__global__ void __launch_bounds__(kBlock)
-update_p_kernel(int vh, const R *__restrict__ r, R *__restrict__ p, CgScalars *S, int check_halt) {
-    if (check_halt && S->halt) return;
-    const R beta = (R)S->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
-        const Vec3<R> rv = load_vec(r, vh, i);
-        Vec3<R> pv = load_vec(p, vh, i);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            pv.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
-            pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
-        }
-        store_vec(p, vh, i, pv);
-    }
+    set_conditions(ctl, S->trips < S->maxiter + 4 ? 1u : 0u, 0u);
 }
 
 // x64 += xh32; xh32 = 0
@@ -122,24 +126,25 @@ __global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restr
     }
 }
 
-// r32 = (float) r64; p32 = r32 + beta p32
+// End of a reliable update: r32 = (float) r64 (mixed precision only), and
+// in the graph solve the loop condition from the flags the FP64 residual set.
 __global__ void __launch_bounds__(kBlock)
-lower_r_update_p_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32, float *__restrict__ p32,
-                        const CgScalars *S) {
-    const float beta = (float)S->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
-        const Vec3<double> rd = load_vec(r64, vh, i);
-        Vec3<float> rv, pv = load_vec(p32, vh, i);
+finish_ru_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32, const CgScalars *S,
+                 const GraphCtl ctl) {
+    if (r32) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+            const Vec3<double> rd = load_vec(r64, vh, i);
+            Vec3<float> rv;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            rv.c[a].re = (float)rd.c[a].re;
-            rv.c[a].im = (float)rd.c[a].im;
-            pv.c[a].re = fmaf(beta, pv.c[a].re, rv.c[a].re);
-            pv.c[a].im = fmaf(beta, pv.c[a].im, rv.c[a].im);
+            for (int a = 0; a < 3; ++a) {
+                rv.c[a].re = (float)rd.c[a].re;
+                rv.c[a].im = (float)rd.c[a].im;
+            }
+            store_vec(r32, vh, i, rv);
         }
-        store_vec(r32, vh, i, rv);
-        store_vec(p32, vh, i, pv);
     }
+    if (ctl.active && blockIdx.x == 0 && threadIdx.x == 0)
+        cudaGraphSetConditional(ctl.loop, (!S->halt && S->trips < S->maxiter + 4) ? 1u : 0u);
 }
 
 template <typename R>
@@ -203,27 +208,18 @@ dot_kernel(int vh, const R *__restrict__ a, const R *__restrict__ b, double *out
     out[1] = t1;
 }
 
-qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, const void *p, const void *ap,
-                            CgScalars *S, cudaStream_t st) {
+qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, void *const pbuf[2], const void *ap,
+                            CgScalars *S, const GraphCtl &ctl, cudaStream_t st) {
     int nb = blas_blocks(lat), vh = (int)lat->vh;
     if (prec == QEX_F64)
-        update_xr_kernel<double><<<nb, kBlock, 0, st>>>(vh, (double *)x, (double *)r, (const double *)p,
-                                                        (const double *)ap, S, lat->partials, lat->counter);
+        update_xr_kernel<double><<<nb, kBlock, 0, st>>>(vh, (double *)x, (double *)r, (double *)pbuf[0],
+                                                        (double *)pbuf[1], (const double *)ap, S, lat->partials,
+                                                        lat->counter, ctl);
     else
-        update_xr_kernel<float><<<nb, kBlock, 0, st>>>(vh, (float *)x, (float *)r, (const float *)p,
-                                                       (const float *)ap, S, lat->partials, lat->counter);
+        update_xr_kernel<float><<<nb, kBlock, 0, st>>>(vh, (float *)x, (float *)r, (float *)pbuf[0],
+                                                       (float *)pbuf[1], (const float *)ap, S, lat->partials,
+                                                       lat->counter, ctl);
     QEX_CHECK_LAUNCH("update_xr_kernel");
-    return QEX_OK;
-}
-
-qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *p, CgScalars *S, int check_halt,
-                           cudaStream_t st) {
-    int nb = blas_blocks(lat), vh = (int)lat->vh;
-    if (prec == QEX_F64)
-        update_p_kernel<double><<<nb, kBlock, 0, st>>>(vh, (const double *)r, (double *)p, S, check_halt);
-    else
-        update_p_kernel<float><<<nb, kBlock, 0, st>>>(vh, (const float *)r, (float *)p, S, check_halt);
-    QEX_CHECK_LAUNCH("update_p_kernel");
     return QEX_OK;
 }
 
@@ -233,10 +229,10 @@ qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream
     return QEX_OK;
 }
 
-qex_status launch_lower_r_update_p(qex_lattice *lat, const double *r64, float *r32, float *p32, CgScalars *S,
-                                   cudaStream_t st) {
-    lower_r_update_p_kernel<<<blas_blocks(lat), kBlock, 0, st>>>((int)lat->vh, r64, r32, p32, S);
-    QEX_CHECK_LAUNCH("lower_r_update_p_kernel");
+qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, const CgScalars *S,
+                            const GraphCtl &ctl, cudaStream_t st) {
+    finish_ru_kernel<<<r32 ? blas_blocks(lat) : 1, kBlock, 0, st>>>((int)lat->vh, r64, r32, S, ctl);
+    QEX_CHECK_LAUNCH("finish_ru_kernel");
     return QEX_OK;
 }
 

@@ -1,21 +1,29 @@
 // cg.cu -- conjugate gradient on A = m^2 - D_eo D_oe (even sites): plain FP64
 // and mixed precision with reliable updates.
 //
-// The iteration keeps alpha, beta and the residual norms on the device: each
-// iteration is four launches (D_oe p; A p with <p, A p>; x, r update with
-// ||r||^2; p update) and none reads anything back.  The host enqueues batches
-// of iterations and reads the scalars once per batch, double-buffered so that
-// the next batch is already queued while the previous flags travel back.
-// Once a kernel sets `halt` (convergence candidate, reliable update due,
-// iteration cap, NaN), the remaining queued iteration kernels return at once.
+// One iteration is three kernels and reads nothing back:
+//   1. p_new = r + beta p_old formed on the fly at every neighbour read,
+//      tmp = D_oe p_new, and p_new stored (two p buffers, chosen by the parity
+//      of the device-side iteration count);
+//   2. A p_new = m^2 p_new - D_eo tmp with <p_new, A p_new> -> alpha;
+//   3. x += alpha p_new, r -= alpha A p_new, ||r||^2 -> beta or a halt flag.
+// alpha, beta and the norms stay in device memory.  By default the whole
+// solve runs as one CUDA graph: a conditional WHILE node around the three
+// kernels, followed inside the loop by a conditional IF node holding the
+// reliable update (FP64 true residual); kernel 3 and the update's last
+// kernel set the two conditions.  The loop ends when the true residual meets
+// tol, on the iteration cap, or on a NaN, and in any case after maxiter + 4
+// trips.  Setting QEX_CG_MODE=host instead enqueues batches of iterations
+// from the host and runs the reliable updates between batches.
 //
-// Mixed precision (inner = F32): x_hat, r_hat, p, A p live in FP32 and the
-// operator runs on FP32 links; when ||r_hat|| falls below delta times its
-// largest value since the last update, or meets tol, the host runs a reliable
-// update: x += x_hat (FP64), r = b - A x with the FP64 operator, r_hat =
-// (float) r, beta from the true ||r||^2, p kept.  Convergence is only ever
-// accepted on the FP64 true residual.
+// Mixed precision (inner = F32 or F32_R12): x_hat, r_hat, p, A p live in FP32
+// and the operator runs on FP32 links; when ||r_hat|| falls below delta times
+// its largest value since the last update, or meets tol, x += x_hat (FP64),
+// r = b - A x with the FP64 operator, r_hat = (float) r, and beta comes from
+// the true ||r||^2; p is kept.  Convergence is only accepted on the FP64 true
+// residual.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "qex_kernels.cuh"
@@ -24,17 +32,18 @@ namespace qex {
 
 qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                              const void *in, const void *out);
+void set_count_launches(bool on);
 
 static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 struct CgBuffers {
-    double *r64, *p64, *ap64, *tmp64;
-    float *xh32, *r32, *p32, *ap32, *tmp32;
+    double *r64, *tmp64, *p64[2], *ap64;
+    float *xh32, *r32, *p32[2], *ap32, *tmp32;
 };
 
 static qex_status carve(qex_lattice *lat, bool mixed, CgBuffers &B) {
     size_t f64 = align256((size_t)lat->vh * 48), f32 = align256((size_t)lat->vh * 24);
-    size_t need = mixed ? 2 * f64 + 5 * f32 : 4 * f64;
+    size_t need = mixed ? 2 * f64 + 6 * f32 : 5 * f64;
     qex_status st = ensure_work(lat, need);
     if (st) return st;
     char *w = (char *)lat->work;
@@ -44,19 +53,17 @@ static qex_status carve(qex_lattice *lat, bool mixed, CgBuffers &B) {
     B.tmp64 = (double *)w;
     w += f64;
     if (mixed) {
-        B.xh32 = (float *)w;
-        w += f32;
-        B.r32 = (float *)w;
-        w += f32;
-        B.p32 = (float *)w;
-        w += f32;
-        B.ap32 = (float *)w;
-        w += f32;
-        B.tmp32 = (float *)w;
+        float **f[] = {&B.xh32, &B.r32, &B.p32[0], &B.p32[1], &B.ap32, &B.tmp32};
+        for (float **q : f) {
+            *q = (float *)w;
+            w += f32;
+        }
     } else {
-        B.p64 = (double *)w;
-        w += f64;
-        B.ap64 = (double *)w;
+        double **d[] = {&B.p64[0], &B.p64[1], &B.ap64};
+        for (double **q : d) {
+            *q = (double *)w;
+            w += f64;
+        }
     }
     return QEX_OK;
 }
@@ -70,11 +77,10 @@ struct Solve {
     const double *b64;
     double *x64;
     CgBuffers B;
-    cudaStream_t st;
 };
 
 // One CG iteration in the inner precision, every kernel halt-checked.
-static qex_status enqueue_iteration(Solve &s) {
+static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t st) {
     qex_lattice *lat = s.lat;
     CgScalars *S = lat->scalars;
     DslashArgs a = {};
@@ -84,35 +90,37 @@ static qex_status enqueue_iteration(Solve &s) {
     a.c3 = s.c3;
     a.S = S;
     a.check_halt = 1;
-    void *p = s.mixed ? (void *)s.B.p32 : (void *)s.B.p64;
     void *tmp = s.mixed ? (void *)s.B.tmp32 : (void *)s.B.tmp64;
     void *ap = s.mixed ? (void *)s.B.ap32 : (void *)s.B.ap64;
     void *x = s.mixed ? (void *)s.B.xh32 : (void *)s.x64;
     void *r = s.mixed ? (void *)s.B.r32 : (void *)s.B.r64;
-    qex_status st;
+    void *pb[2] = {s.mixed ? (void *)s.B.p32[0] : (void *)s.B.p64[0],
+                   s.mixed ? (void *)s.B.p32[1] : (void *)s.B.p64[1]};
+    qex_status err;
     a.out_parity = 1;
-    a.in = p;
     a.out = tmp;
-    a.epi = EPI_PLAIN;
-    if ((st = launch_dslash(lat, a, s.st))) return st;
+    a.epi = EPI_PUPD;
+    a.r = r;
+    a.pbuf[0] = pb[0];
+    a.pbuf[1] = pb[1];
+    if ((err = launch_dslash(lat, a, st))) return err;
     a.out_parity = 0;
     a.in = tmp;
     a.out = ap;
     a.epi = EPI_NORMAL;
-    a.q = p;
+    a.qsel = 1;
     a.m2 = s.m2;
-    if ((st = launch_dslash(lat, a, s.st))) return st;
-    if ((st = launch_update_xr(lat, a.prec, x, r, p, ap, S, s.st))) return st;
-    return launch_update_p(lat, a.prec, r, p, S, 1, s.st);
+    if ((err = launch_dslash(lat, a, st))) return err;
+    return launch_update_xr(lat, a.prec, x, r, pb, ap, S, ctl, st);
 }
 
 // FP64 true residual r64 = b - A x64 (after folding x_hat into x64), then the
-// inner residual and search direction from it.
-static qex_status enqueue_reliable_update(Solve &s) {
+// inner residual from it.
+static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStream_t st) {
     qex_lattice *lat = s.lat;
     CgScalars *S = lat->scalars;
-    qex_status st;
-    if (s.mixed && (st = launch_accum_x(lat, s.x64, s.B.xh32, s.st))) return st;
+    qex_status err;
+    if (s.mixed && (err = launch_accum_x(lat, s.x64, s.B.xh32, st))) return err;
     DslashArgs a = {};
     a.prec = QEX_F64;
     a.fat = s.fat64;
@@ -122,7 +130,7 @@ static qex_status enqueue_reliable_update(Solve &s) {
     a.in = s.x64;
     a.out = s.B.tmp64;
     a.epi = EPI_PLAIN;
-    if ((st = launch_dslash(lat, a, s.st))) return st;
+    if ((err = launch_dslash(lat, a, st))) return err;
     a.out_parity = 0;
     a.in = s.B.tmp64;
     a.out = s.B.r64;
@@ -131,22 +139,128 @@ static qex_status enqueue_reliable_update(Solve &s) {
     a.b = s.b64;
     a.m2 = s.m2;
     a.S = S;
-    if ((st = launch_dslash(lat, a, s.st))) return st;
-    if (s.mixed) return launch_lower_r_update_p(lat, s.B.r64, s.B.r32, s.B.p32, S, s.st);
-    return launch_update_p(lat, QEX_F64, s.B.r64, s.B.p64, S, 0, s.st);
+    if ((err = launch_dslash(lat, a, st))) return err;
+    return launch_finish_ru(lat, s.B.r64, s.mixed ? s.B.r32 : nullptr, S, ctl, st);
 }
 
-static qex_status fetch_scalars(Solve &s, int slot) {
-    QEX_CUDA(cudaMemcpyAsync(slot ? s.lat->scalars_host2 : s.lat->scalars_host, s.lat->scalars,
-                             sizeof(CgScalars), cudaMemcpyDeviceToHost, s.st));
-    QEX_CUDA(cudaEventRecord(slot ? s.lat->ev1 : s.lat->ev0, s.st));
+static qex_status fetch_scalars(qex_lattice *lat, int slot, cudaStream_t st) {
+    QEX_CUDA(cudaMemcpyAsync(slot ? lat->scalars_host2 : lat->scalars_host, lat->scalars, sizeof(CgScalars),
+                             cudaMemcpyDeviceToHost, st));
+    QEX_CUDA(cudaEventRecord(slot ? lat->ev1 : lat->ev0, st));
     return QEX_OK;
 }
 
-static qex_status wait_scalars(Solve &s, int slot) {
-    QEX_CUDA(cudaEventSynchronize(slot ? s.lat->ev1 : s.lat->ev0));
+static qex_status wait_scalars(qex_lattice *lat, int slot) {
+    QEX_CUDA(cudaEventSynchronize(slot ? lat->ev1 : lat->ev0));
     return QEX_OK;
 }
+
+// ------------------------------------------------------------- graph solve
+
+// An instantiated solve graph, reusable while every pointer and constant
+// baked into its kernels stays the same.
+struct CgGraph {
+    qex_prec inner;
+    const void *fat64, *lng64, *fat32, *lng32;
+    double c3, m2;
+    const void *b64, *x64, *work;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    unsigned long long kernels_per_trip, kernels_per_ru;
+};
+
+static bool same_key(const CgGraph *g, const Solve &s) {
+    return g && g->inner == s.inner && g->fat64 == s.fat64 && g->lng64 == s.lng64 && g->fat32 == s.fat32 &&
+           g->lng32 == s.lng32 && g->c3 == s.c3 && g->m2 == s.m2 && g->b64 == s.b64 && g->x64 == s.x64 &&
+           g->work == s.lat->work;
+}
+
+static void drop_graph(CgGraph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+static qex_status build_graph(Solve &s, CgGraph **out) {
+    *out = nullptr;
+    CgGraph *G = new CgGraph;
+    memset(G, 0, sizeof(*G));
+    G->inner = s.inner;
+    G->fat64 = s.fat64;
+    G->lng64 = s.lng64;
+    G->fat32 = s.fat32;
+    G->lng32 = s.lng32;
+    G->c3 = s.c3;
+    G->m2 = s.m2;
+    G->b64 = s.b64;
+    G->x64 = s.x64;
+    G->work = s.lat->work;
+    G->kernels_per_trip = 3;
+    G->kernels_per_ru = s.mixed ? 4 : 3;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaSuccess;
+    qex_status st = QEX_OK;
+    set_count_launches(false);
+    do {
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) break;
+        if ((e = cudaGraphCreate(&G->graph, 0))) break;
+        GraphCtl ctl = {};
+        ctl.active = 1;
+        if ((e = cudaGraphConditionalHandleCreate(&ctl.loop, G->graph, 1, cudaGraphCondAssignDefault))) break;
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = ctl.loop;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        if ((e = cudaGraphAddNode(&wnode, G->graph, nullptr, nullptr, 0, &wp))) break;
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        if ((e = cudaGraphConditionalHandleCreate(&ctl.ru, body, 0, 0))) break;
+        // loop body: the three iteration kernels, then IF (reliable update)
+        if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
+        st = enqueue_iteration(s, ctl, cs);
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t capg = nullptr;
+        cudaGraphNodeParams ip = {};
+        cudaGraphNode_t inode = nullptr;
+        if (!st) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps);
+        if (!st && !e) {
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = ctl.ru;
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            e = cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip);
+        }
+        if (!st && !e) e = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+        if (st) break;
+        if (e || (e = e2)) break;
+        // IF body: the reliable update
+        if ((e = cudaStreamBeginCaptureToGraph(cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeRelaxed)))
+            break;
+        st = enqueue_reliable_update(s, ctl, cs);
+        e2 = cudaStreamEndCapture(cs, &captured);
+        if (st) break;
+        if ((e = e2)) break;
+        if ((e = cudaGraphInstantiate(&G->exec, G->graph, 0))) break;
+    } while (0);
+    set_count_launches(true);
+    if (cs) cudaStreamDestroy(cs);
+    if (st || e) {
+        drop_graph(G);
+        if (!st) st = cuda_fail(e, "building the CG graph");
+        return st;
+    }
+    *out = G;
+    return QEX_OK;
+}
+
+void free_cg_graph(void *g) { drop_graph((CgGraph *)g); }
 
 }  // namespace qex
 
@@ -172,8 +286,9 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     }
     qex_lattice *lat = const_cast<qex_lattice *>(latc);
     if ((st = ensure_scratch(lat))) return st;
-    // two pinned scalar slots for the double-buffered readback
     if (!lat->scalars_host2) QEX_CUDA(cudaMallocHost(&lat->scalars_host2, sizeof(CgScalars)));
+    const char *mode = getenv("QEX_CG_MODE");
+    const bool use_graph = !(mode && strcmp(mode, "host") == 0);
 
     Solve s;
     s.lat = lat;
@@ -181,19 +296,27 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     s.inner = inner;
     s.fat64 = fat64;
     s.lng64 = lng64;
-    s.fat32 = fat32;
+    s.fat32 = mixed ? fat32 : nullptr;
     s.lng32 = mixed ? lng32 : nullptr;
     s.c3 = c_naik;
     s.m2 = mass * mass;
     s.b64 = (const double *)b64;
     s.x64 = (double *)x64;
-    s.st = as_stream(stream);
+    const cudaStream_t cst = as_stream(stream);
     if ((st = carve(lat, mixed, s.B))) return st;
+    if (use_graph && !same_key((CgGraph *)lat->cg_graph, s)) {
+        QEX_CUDA(cudaStreamSynchronize(cst));
+        drop_graph((CgGraph *)lat->cg_graph);
+        lat->cg_graph = nullptr;
+        CgGraph *G;
+        if ((st = build_graph(s, &G))) return st;
+        lat->cg_graph = G;
+    }
 
     cudaEvent_t t0, t1;
     QEX_CUDA(cudaEventCreate(&t0));
     QEX_CUDA(cudaEventCreate(&t1));
-    QEX_CUDA(cudaEventRecord(t0, s.st));
+    QEX_CUDA(cudaEventRecord(t0, cst));
 
     CgScalars init;
     memset(&init, 0, sizeof(init));
@@ -201,74 +324,73 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     init.delta2 = mixed ? delta * delta : 0.0;
     init.maxiter = maxiter;
     CgScalars *h0 = lat->scalars_host, *h1 = lat->scalars_host2;
-    QEX_CUDA(cudaStreamSynchronize(s.st));  // the pinned slots are free
+    QEX_CUDA(cudaStreamSynchronize(cst));  // the pinned slots are free
     *h0 = init;
-    QEX_CUDA(cudaMemcpyAsync(lat->scalars, h0, sizeof(CgScalars), cudaMemcpyHostToDevice, s.st));
+    QEX_CUDA(cudaMemcpyAsync(lat->scalars, h0, sizeof(CgScalars), cudaMemcpyHostToDevice, cst));
     size_t fbytes = (size_t)lat->vh * (mixed ? 24 : 48);
-    QEX_CUDA(cudaMemsetAsync(mixed ? (void *)s.B.p32 : (void *)s.B.p64, 0, fbytes, s.st));
-    if (mixed) QEX_CUDA(cudaMemsetAsync(s.B.xh32, 0, fbytes, s.st));
-    if ((st = launch_norm2(lat, QEX_F64, b64, nullptr, lat->scalars, s.st))) return st;
-    if ((st = enqueue_reliable_update(s))) return st;
-    QEX_CUDA(cudaMemcpyAsync(h0, lat->scalars, sizeof(CgScalars), cudaMemcpyDeviceToHost, s.st));
-    QEX_CUDA(cudaStreamSynchronize(s.st));
+    for (int k = 0; k < 2; ++k)
+        QEX_CUDA(cudaMemsetAsync(mixed ? (void *)s.B.p32[k] : (void *)s.B.p64[k], 0, fbytes, cst));
+    if (mixed) QEX_CUDA(cudaMemsetAsync(s.B.xh32, 0, fbytes, cst));
+    const GraphCtl off = {};
+    if ((st = launch_norm2(lat, QEX_F64, b64, nullptr, lat->scalars, cst))) return st;
+    if ((st = enqueue_reliable_update(s, off, cst))) return st;
+    if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
 
     qex_status result = QEX_OK;
     CgScalars cur = *h0;
     if (cur.bb == 0.0) {
-        QEX_CUDA(cudaMemsetAsync(x64, 0, (size_t)lat->vh * 48, s.st));
+        QEX_CUDA(cudaMemsetAsync(x64, 0, (size_t)lat->vh * 48, cst));
         cur.done = 1;
         cur.true_rr = 0.0;
     } else if (!isfinite(cur.bb) || cur.error) {
         set_error("NaN/Inf in the source or the initial residual");
         result = QEX_ERR_NAN;
-    } else {
+    } else if (!cur.done && !cur.halt && use_graph) {
+        CgGraph *G = (CgGraph *)lat->cg_graph;
+        QEX_CUDA(cudaGraphLaunch(G->exec, cst));
+        if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
+        cur = *h0;
+        const unsigned long long rus = cur.reliable_updates > 1 ? cur.reliable_updates - 1 : 0;
+        note_launches(G->kernels_per_trip * (unsigned long long)cur.trips + G->kernels_per_ru * rus);
+    } else if (!cur.done && !cur.halt) {
         const int batch = 8;
         while (!cur.done && !cur.error) {
-            if (cur.halt) {
-                if (cur.iters >= maxiter) {
-                    set_error("CG did not converge in %d iterations", maxiter);
-                    result = QEX_ERR_NOT_CONVERGED;
-                    break;
-                }
-            }
             // iterate until a kernel halts; slot k&1 holds the scalars after batch k
             int k = 0;
             for (int j = 0; j < batch; ++j)
-                if ((st = enqueue_iteration(s))) return st;
-            if ((st = fetch_scalars(s, 0))) return st;
+                if ((st = enqueue_iteration(s, off, cst))) return st;
+            if ((st = fetch_scalars(lat, 0, cst))) return st;
             for (;;) {
                 for (int j = 0; j < batch; ++j)
-                    if ((st = enqueue_iteration(s))) return st;
-                if ((st = fetch_scalars(s, (k + 1) & 1))) return st;
-                if ((st = wait_scalars(s, k & 1))) return st;
+                    if ((st = enqueue_iteration(s, off, cst))) return st;
+                if ((st = fetch_scalars(lat, (k + 1) & 1, cst))) return st;
+                if ((st = wait_scalars(lat, k & 1))) return st;
                 cur = (k & 1) ? *h1 : *h0;
                 ++k;
                 if (cur.halt) break;
             }
-            if ((st = wait_scalars(s, k & 1))) return st;  // drain the queued batch
+            if ((st = wait_scalars(lat, k & 1))) return st;  // drain the queued batch
             cur = (k & 1) ? *h1 : *h0;
-            if (cur.error) break;
-            if (!cur.need_ru) {  // halt without a cause: never set by the kernels
-                set_error("internal error: CG halted without a reason");
-                result = QEX_ERR_ARG;
-                break;
-            }
-            if ((st = enqueue_reliable_update(s))) return st;
-            if ((st = fetch_scalars(s, 0))) return st;
-            if ((st = wait_scalars(s, 0))) return st;
+            if (cur.error || !cur.need_ru) break;
+            if ((st = enqueue_reliable_update(s, off, cst))) return st;
+            if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
             cur = *h0;
-            if (!cur.done && !cur.error && cur.iters >= maxiter) {
-                set_error("CG did not converge in %d iterations", maxiter);
-                result = QEX_ERR_NOT_CONVERGED;
-                break;
-            }
-        }
-        if (cur.error && result == QEX_OK) {
-            set_error(cur.error == 2 ? "CG breakdown: <p, A p> <= 0" : "NaN/Inf in a CG reduction");
-            result = QEX_ERR_NAN;
+            if (!cur.done && !cur.error && cur.iters >= maxiter) break;
         }
     }
-    QEX_CUDA(cudaEventRecord(t1, s.st));
+    if (result == QEX_OK && !cur.done) {
+        if (cur.error) {
+            set_error(cur.error == 2 ? "CG breakdown: <p, A p> <= 0" : "NaN/Inf in a CG reduction");
+            result = QEX_ERR_NAN;
+        } else if (cur.iters >= maxiter) {
+            set_error("CG did not converge in %d iterations", maxiter);
+            result = QEX_ERR_NOT_CONVERGED;
+        } else {
+            set_error("internal error: CG stopped without a reason (iters %d, trips %d)", cur.iters, cur.trips);
+            result = QEX_ERR_ARG;
+        }
+    }
+    QEX_CUDA(cudaEventRecord(t1, cst));
     QEX_CUDA(cudaEventSynchronize(t1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, t0, t1);

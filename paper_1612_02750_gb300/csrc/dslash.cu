@@ -24,18 +24,65 @@ __device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int
         return load_link(base, vh, p, mu, i);
 }
 
+template <typename R>
+struct DsParams {
+    Geom g;
+    const R *fat;
+    const R *lng;
+    R c3;
+    int p;              // output parity
+    const R *in;
+    R *out;
+    const R *q;
+    const double *b;
+    R m2;
+    CgScalars *S;
+    int check_halt;
+    const R *r;         // EPI_PUPD
+    R *pbuf0, *pbuf1;   // p ping-pong
+    int qsel;
+    double *partials;
+    unsigned int *counter;
+};
+
+// Input colour vector at index j: the field itself, or (EPI_PUPD) the new
+// search direction r + beta p_old formed on the fly.
+template <typename R, int EPI>
+__device__ __forceinline__ Vec3<R> load_in(const DsParams<R> &P, size_t vh, int j, const R *pold, R beta) {
+    if constexpr (EPI == EPI_PUPD) {
+        const Vec3<R> rv = load_vec(P.r, vh, j), pv = load_vec(pold, vh, j);
+        Vec3<R> v;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+            v.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+        }
+        return v;
+    } else {
+        return load_vec(P.in, vh, j);
+    }
+}
+
 template <typename R, int FMT, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kBlock)
-dslash_kernel(Geom g, const R *__restrict__ fat, const R *__restrict__ lng, R c3, int p,
-              const R *__restrict__ in, R *__restrict__ out, const R *__restrict__ q,
-              const double *__restrict__ b, R m2, CgScalars *S, int check_halt,
-              double *partials, unsigned int *counter) {
+__global__ void __launch_bounds__(kBlock) dslash_kernel(const DsParams<R> P) {
     __shared__ double smem[32];
     __shared__ unsigned int is_last;
-    if (check_halt && S->halt) return;  // uniform over the grid
+    if (P.check_halt && P.S->halt) return;  // uniform over the grid
 
+    const Geom &g = P.g;
     const size_t vh = (size_t)g.vh;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = P.p;
+    // direction buffers by iteration parity (read before any block can change it)
+    const R *pold = nullptr;
+    R *pnew = nullptr;
+    R beta = R(0);
+    if constexpr (EPI == EPI_PUPD) {
+        const int it = P.S->iters;
+        pold = (it & 1) ? P.pbuf1 : P.pbuf0;
+        pnew = (it & 1) ? P.pbuf0 : P.pbuf1;
+        beta = (R)P.S->beta;
+    }
     double part = 0.0;
     if (i < g.vh) {
         const Site s = site_of(g, p, i);
@@ -47,114 +94,141 @@ dslash_kernel(Geom g, const R *__restrict__ fat, const R *__restrict__ lng, R c3
             const R eta = eta_bit(s, mu) ? R(-1) : R(1);
             {   // + eta b U_mu(x) psi(x + mu)
                 const int j = hop_index(g, s, mu, 1);
-                const Mat3<R> u = load_fat<R, FMT>(fat, vh, p, mu, i);
-                const Vec3<R> v = load_vec(in, vh, j);
+                const Mat3<R> u = load_fat<R, FMT>(P.fat, vh, p, mu, i);
+                const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
                 acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, v);
             }
             {   // - eta b U_mu(x - mu)^+ psi(x - mu)
                 const int j = hop_index(g, s, mu, -1);
-                const Mat3<R> u = load_fat<R, FMT>(fat, vh, 1 - p, mu, j);
-                const Vec3<R> v = load_vec(in, vh, j);
+                const Mat3<R> u = load_fat<R, FMT>(P.fat, vh, 1 - p, mu, j);
+                const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
                 acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, v);
             }
             if (NAIK) {
-                const R e3 = c3 * eta;
+                const R e3 = P.c3 * eta;
                 {
                     const int j = hop_index(g, s, mu, 3);
-                    const Mat3<R> u = load_link(lng, vh, p, mu, i);
-                    const Vec3<R> v = load_vec(in, vh, j);
+                    const Mat3<R> u = load_link(P.lng, vh, p, mu, i);
+                    const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
                     acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, v);
                 }
                 {
                     const int j = hop_index(g, s, mu, -3);
-                    const Mat3<R> u = load_link(lng, vh, 1 - p, mu, j);
-                    const Vec3<R> v = load_vec(in, vh, j);
+                    const Mat3<R> u = load_link(P.lng, vh, 1 - p, mu, j);
+                    const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
                     acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, v);
                 }
             }
         }
-        if (EPI == EPI_PLAIN) {
-            store_vec(out, vh, i, acc);
-        } else if (EPI == EPI_NORMAL) {
+        if constexpr (EPI == EPI_PLAIN) {
+            store_vec(P.out, vh, i, acc);
+        } else if constexpr (EPI == EPI_PUPD) {
+            store_vec(P.out, vh, i, acc);
+            // this thread also owns index i of the other parity's direction
+            store_vec(pnew, vh, i, load_in<R, EPI>(P, vh, i, pold, beta));
+        } else if constexpr (EPI == EPI_NORMAL) {
             // out = m^2 q - D in;  part = Re <q, out>
+            const R *q = P.q;
+            if (P.qsel) q = (P.S->iters & 1) ? P.pbuf0 : P.pbuf1;  // the new direction
             const Vec3<R> qv = load_vec(q, vh, i);
             Vec3<R> o;
             R d = R(0);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                o.c[a].re = fma(m2, qv.c[a].re, -acc.c[a].re);
-                o.c[a].im = fma(m2, qv.c[a].im, -acc.c[a].im);
+                o.c[a].re = fma(P.m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = fma(P.m2, qv.c[a].im, -acc.c[a].im);
                 d = fma(qv.c[a].re, o.c[a].re, d);
                 d = fma(qv.c[a].im, o.c[a].im, d);
             }
-            store_vec(out, vh, i, o);
+            store_vec(P.out, vh, i, o);
             part = (double)d;
         } else {
             // out = b - m^2 q + D in;  part = ||out||^2   (FP64 only)
-            const Vec3<R> qv = load_vec(q, vh, i);
-            const Vec3<double> bv = load_vec(b, vh, i);
+            const Vec3<R> qv = load_vec(P.q, vh, i);
+            const Vec3<double> bv = load_vec(P.b, vh, i);
             Vec3<R> o;
             double d = 0.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                o.c[a].re = (R)bv.c[a].re - fma(m2, qv.c[a].re, -acc.c[a].re);
-                o.c[a].im = (R)bv.c[a].im - fma(m2, qv.c[a].im, -acc.c[a].im);
+                o.c[a].re = (R)bv.c[a].re - fma(P.m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = (R)bv.c[a].im - fma(P.m2, qv.c[a].im, -acc.c[a].im);
                 d = fma((double)o.c[a].re, (double)o.c[a].re, d);
                 d = fma((double)o.c[a].im, (double)o.c[a].im, d);
             }
-            store_vec(out, vh, i, o);
+            store_vec(P.out, vh, i, o);
             part = d;
         }
     }
-    if (EPI == EPI_PLAIN || S == nullptr) return;  // S is uniform over the grid
-
-    // Deterministic grid reduction: block sums -> partials; the last block to
-    // finish sums the partials in index order and updates the CG scalars.
-    const double bs = block_sum(part, smem);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = bs;
-        __threadfence();
-        unsigned int t = atomicAdd(counter, 1u);
-        is_last = (t == gridDim.x - 1) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    const double tot = block_sum_partials(partials, gridDim.x, smem);
-    if (threadIdx.x != 0) return;
-    *counter = 0u;
-    if (EPI == EPI_NORMAL) {
-        S->pAp = tot;
-        if (!(tot > 0.0) || !isfinite(tot)) {
-            S->error = isfinite(tot) ? 2 : 1;
-            S->halt = 1;
-        } else {
-            S->alpha = S->rr / tot;
-        }
+    if constexpr (EPI == EPI_PLAIN || EPI == EPI_PUPD) {
+        return;
     } else {
-        // FP64 true residual: accept convergence or continue with beta from it
-        S->true_rr = tot;
-        S->reliable_updates += 1;
-        if (!isfinite(tot)) {
-            S->error = 1;
-            S->halt = 1;
-            return;
+        CgScalars *S = P.S;
+        if (S == nullptr) return;  // uniform over the grid
+
+        // Deterministic grid reduction: block sums -> partials; the last block
+        // to finish sums the partials in index order and updates the CG scalars.
+        const double bs = block_sum(part, smem);
+        if (threadIdx.x == 0) {
+            P.partials[blockIdx.x] = bs;
+            __threadfence();
+            unsigned int t = atomicAdd(P.counter, 1u);
+            is_last = (t == gridDim.x - 1) ? 1u : 0u;
         }
-        S->beta = S->rr > 0.0 ? tot / S->rr : 0.0;
-        S->rr = tot;
-        S->rmax2 = tot;
-        S->need_ru = 0;
-        S->done = tot <= S->stop2 ? 1 : 0;
-        S->halt = (S->done || S->iters >= S->maxiter) ? 1 : 0;
+        __syncthreads();
+        if (!is_last) return;
+        __threadfence();
+        const double tot = block_sum_partials(P.partials, gridDim.x, smem);
+        if (threadIdx.x != 0) return;
+        *P.counter = 0u;
+        if constexpr (EPI == EPI_NORMAL) {
+            S->pAp = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) {
+                S->error = isfinite(tot) ? 2 : 1;
+                S->halt = 1;
+            } else {
+                S->alpha = S->rr / tot;
+            }
+        } else {
+            // FP64 true residual: accept convergence, or continue with beta from it
+            S->true_rr = tot;
+            S->reliable_updates += 1;
+            if (!isfinite(tot)) {
+                S->error = 1;
+                S->halt = 1;
+                return;
+            }
+            S->beta = S->rr > 0.0 ? tot / S->rr : 0.0;
+            S->rr = tot;
+            S->rmax2 = tot;
+            S->need_ru = 0;
+            S->done = tot <= S->stop2 ? 1 : 0;
+            S->halt = (S->done || S->iters >= S->maxiter) ? 1 : 0;
+        }
     }
 }
 
 template <typename R, int FMT, bool NAIK, int EPI>
 static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
-    int nb = blocks_for(lat->vh);
-    dslash_kernel<R, FMT, NAIK, EPI><<<nb, kBlock, 0, st>>>(
-        lat->geom, (const R *)a.fat, (const R *)a.lng, (R)a.c3, a.out_parity, (const R *)a.in, (R *)a.out,
-        (const R *)a.q, a.b, (R)a.m2, a.S, a.check_halt, lat->partials, lat->counter);
+    DsParams<R> P;
+    P.g = lat->geom;
+    P.fat = (const R *)a.fat;
+    P.lng = (const R *)a.lng;
+    P.c3 = (R)a.c3;
+    P.p = a.out_parity;
+    P.in = (const R *)a.in;
+    P.out = (R *)a.out;
+    P.q = (const R *)a.q;
+    P.b = a.b;
+    P.m2 = (R)a.m2;
+    P.S = a.S;
+    P.check_halt = a.check_halt;
+    P.r = (const R *)a.r;
+    P.pbuf0 = (R *)a.pbuf[0];
+    P.pbuf1 = (R *)a.pbuf[1];
+    P.qsel = a.qsel;
+    P.partials = lat->partials;
+    P.counter = lat->counter;
+    dslash_kernel<R, FMT, NAIK, EPI><<<blocks_for(lat->vh), kBlock, 0, st>>>(P);
 }
 
 template <typename R, int FMT, bool NAIK>
@@ -163,6 +237,8 @@ static void launch_epi(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
         launch_t<R, FMT, NAIK, EPI_PLAIN>(lat, a, st);
     else if (a.epi == EPI_NORMAL)
         launch_t<R, FMT, NAIK, EPI_NORMAL>(lat, a, st);
+    else if (a.epi == EPI_PUPD)
+        launch_t<R, FMT, NAIK, EPI_PUPD>(lat, a, st);
     else if constexpr (std::is_same<R, double>::value)
         launch_t<R, FMT, NAIK, EPI_RESID>(lat, a, st);
 }

@@ -13,7 +13,13 @@ namespace qex {
 static thread_local char g_err[512] = "";
 static std::atomic<unsigned long long> g_launches(0);
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool g_count = true;  // off while a graph is being captured
+
+void note_launch() {
+    if (g_count) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_count_launches(bool on) { g_count = on; }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -90,6 +96,10 @@ qex_status ensure_scratch(qex_lattice *lat) {
 
 qex_status ensure_work(qex_lattice *lat, size_t bytes) {
     if (lat->work_bytes >= bytes) return QEX_OK;
+    if (lat->cg_graph) {  // its kernels point into the old buffer
+        free_cg_graph(lat->cg_graph);
+        lat->cg_graph = nullptr;
+    }
     if (lat->work) {
         QEX_CUDA(cudaDeviceSynchronize());
         QEX_CUDA(cudaFree(lat->work));
@@ -173,7 +183,7 @@ qex_status qex_lattice_create(const int dims[4], int antiperiodic_t, qex_lattice
 qex_status qex_lattice_destroy(qex_lattice *lat) {
     if (!lat) return QEX_OK;
     qex_status st = QEX_OK;
-    if (lat->partials || lat->work) {
+    if (lat->partials || lat->work || lat->host_work) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize in destroy");
     }
@@ -185,6 +195,7 @@ qex_status qex_lattice_destroy(qex_lattice *lat) {
     if (lat->scalars_host2) cudaFreeHost(lat->scalars_host2);
     if (lat->work) cudaFree(lat->work);
     if (lat->host_work) cudaFree(lat->host_work);
+    if (lat->cg_graph) free_cg_graph(lat->cg_graph);
     if (lat->ev0) cudaEventDestroy(lat->ev0);
     if (lat->ev1) cudaEventDestroy(lat->ev1);
     delete lat;

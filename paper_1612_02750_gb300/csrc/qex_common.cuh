@@ -337,6 +337,7 @@ struct qex_lattice {
     size_t work_bytes;
     void *host_work;           // staging of qex_cg_host
     size_t host_work_bytes;
+    void *cg_graph;            // cached CUDA graph of the last CG solve
     cudaEvent_t ev0, ev1;
 };
 

@@ -13,28 +13,37 @@ struct CgScalars {
     double rr;        // ||r||^2 of the iterated residual (FP64 accumulation)
     double pAp;       // Re <p, A p>
     double alpha;     // rr / pAp
-    double beta;      // rr_new / rr
+    double beta;      // rr_new / rr (used by the next direction update)
     double bb;        // ||b||^2
     double tol2;      // tol^2
     double stop2;     // tol^2 * bb
     double delta2;    // reliable-update threshold factor delta^2 (0: only at convergence)
     double rmax2;     // max ||r||^2 since the last reliable update
     double true_rr;   // ||b - A x||^2 from the last FP64 recomputation
-    int iters;        // completed iterations
+    int iters;        // completed iterations; its parity selects the current p buffer
     int maxiter;
     int done;         // true residual met tol
     int need_ru;      // iterated residual calls for an FP64 recomputation
     int halt;         // done | need_ru | error: iteration kernels return at once
     int error;        // 1: NaN/Inf in a reduction, 2: <p, Ap> <= 0
     int reliable_updates;
-    int pad;
+    int trips;        // executions of the update kernel (graph loop guard)
 };
 
-// Epilogues of the Dslash kernel.
+// Conditional-node handles of the CUDA-graph solve (active = 0 outside it).
+// The loop never runs more than maxiter + 4 trips (CgScalars::trips).
+struct GraphCtl {
+    int active;
+    cudaGraphConditionalHandle loop;  // while: run another iteration
+    cudaGraphConditionalHandle ru;    // if: run a reliable update now
+};
+
+// Epilogues / variants of the Dslash kernel.
 enum Epilogue {
     EPI_PLAIN = 0,   // out = D in
-    EPI_NORMAL = 1,  // out = m^2 q - D in; Re<q, out> -> pAp, alpha   (CG: q = p)
-    EPI_RESID = 2    // out = b - m^2 q + D in; ||out||^2 -> true_rr, flags (CG: q = x)
+    EPI_NORMAL = 1,  // out = m^2 q - D in; Re<q, out> -> pAp, alpha   (CG: q = new p)
+    EPI_RESID = 2,   // out = b - m^2 q + D in; ||out||^2 -> true_rr, flags (CG: q = x), FP64 only
+    EPI_PUPD = 3     // in = r + beta p_old (formed on the fly), out = D in, p_new = r + beta p_old stored
 };
 
 struct DslashArgs {
@@ -43,30 +52,32 @@ struct DslashArgs {
     const void *lng;     // NULL: no Naik term
     double c3;
     int out_parity;
-    const void *in;
+    const void *in;      // EPI_PLAIN / NORMAL / RESID
     void *out;
     int epi;
-    const void *q;       // EPI_NORMAL / EPI_RESID
+    const void *q;       // EPI_NORMAL / EPI_RESID (ignored when qsel)
     const double *b;     // EPI_RESID (FP64 half field)
     double m2;
-    CgScalars *S;        // EPI_NORMAL / EPI_RESID / halt check
+    CgScalars *S;        // EPI_NORMAL / EPI_RESID / halt check / buffer selection
     int check_halt;
+    // CG direction ping-pong: p_old = pbuf[iters & 1], p_new = pbuf[(iters + 1) & 1]
+    const void *r;       // EPI_PUPD
+    void *pbuf[2];       // EPI_PUPD, and EPI_NORMAL when qsel
+    int qsel;            // EPI_NORMAL: q = p_new
 };
 
 qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
 
-// BLAS-1 pieces of the CG iteration (grid-stride, fixed grid per lattice).
-// x += alpha p; r -= alpha ap; ||r||^2 -> S (rr, beta, flags).
-qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, const void *p,
-                            const void *ap, CgScalars *S, cudaStream_t st);
-// p = r + beta p  (halt-checked when check_halt).
-qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *p, CgScalars *S,
-                           int check_halt, cudaStream_t st);
+// x += alpha p_new; r -= alpha ap; ||r||^2 -> S (rr, beta, flags); sets the
+// graph conditions when ctl.active.
+qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, void *const pbuf[2],
+                            const void *ap, CgScalars *S, const GraphCtl &ctl, cudaStream_t st);
 // x64 += (double) xh32; xh32 = 0.
 qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st);
-// r32 = (float) r64; p32 = r32 + beta p32.
-qex_status launch_lower_r_update_p(qex_lattice *lat, const double *r64, float *r32, float *p32,
-                                   CgScalars *S, cudaStream_t st);
+// r32 = (float) r64 (r32 may be NULL: only the graph condition is set);
+// loop condition = !halt when ctl.active.
+qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, const CgScalars *S,
+                            const GraphCtl &ctl, cudaStream_t st);
 // ||f||^2 -> *out (FP64, fixed order); if S, also S->bb and S->stop2.
 qex_status launch_norm2(qex_lattice *lat, qex_prec prec, const void *f, double *out, CgScalars *S,
                         cudaStream_t st);
@@ -75,5 +86,8 @@ qex_status launch_dot(qex_lattice *lat, qex_prec prec, const void *a, const void
                       cudaStream_t st);
 
 int blas_blocks(const qex_lattice *lat);
+void note_launches(unsigned long long n);
+void set_count_launches(bool on);
+void free_cg_graph(void *g);
 
 }  // namespace qex

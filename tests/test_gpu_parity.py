@@ -218,6 +218,28 @@ def test_cg_parity(q, oracle_mod, naik, inner):
         assert stats["reliable_updates"] >= 1
 
 
+@pytest.mark.parametrize("inner", ["f64", "f32r12"])
+def test_cg_graph_and_host_loop_agree_bitwise(q, oracle_mod, inner, monkeypatch):
+    """The single-graph solve (conditional while/if nodes) and the host-driven
+    batched loop run the same kernels in the same order: identical bits."""
+    dims = (8, 4, 6, 8)
+    m = 0.05
+    S = Setup(q, dims, False, seed=25)
+    b = S.psi.copy()
+    b[~fg.even_mask(dims)] = 0
+    monkeypatch.setenv("QEX_CG_MODE", "host")
+    st_h, stats_h, x_h = _cg(q, S, inner, m, b, delta=0.05)
+    monkeypatch.setenv("QEX_CG_MODE", "graph")
+    st_g, stats_g, x_g = _cg(q, S, inner, m, b, delta=0.05)
+    assert st_h == st_g == 0
+    assert stats_h["iters"] == stats_g["iters"] and stats_h["reliable_updates"] == stats_g["reliable_updates"]
+    assert np.array_equal(x_h, x_g)
+    assert oracle_mod.true_residual(dims, S.u, b, x_g, m) <= 1.05e-10
+    # maxiter reached inside the graph loop
+    st, stats, _ = _cg(q, S, inner, m, b, maxiter=7)
+    assert st == 5 and stats["iters"] == 7
+
+
 def test_cg_workload_4x4_fp64_matches_oracle_iterations(q, oracle_mod):
     """4^4, Haar links, m = 0.1: FP64 CG reaches 1e-10 with the oracle's
     iteration count up to rounding-driven differences."""
