@@ -49,17 +49,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every .cu under csrc/ and link libqex_gpu.so; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=None, out_dir=None) -> str:
+    """Compile every .cu under csrc/ and link libqex_gpu.so; returns its path.
+
+    ``extra_flags`` (e.g. ``-DQEX_DSLASH_BLOCK=128``) and ``out_dir`` build a
+    variant library elsewhere, for launch-shape sweeps."""
+    lib = LIB if out_dir is None else os.path.join(out_dir, "libqex_gpu.so")
+    build_dir = BUILD if out_dir is None else out_dir
+    if not force and out_dir is None and up_to_date():
         return LIB
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     flags = ARCH + NVCC_FLAGS + list(extra_flags or [])
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc] + flags + ["-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
         if verbose:
@@ -75,14 +80,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(os.path.basename(f) for f in failed))
     cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath", "-Xlinker", cudalib]
     if verbose:
         print(" ".join(link), flush=True)
     subprocess.check_call(link)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

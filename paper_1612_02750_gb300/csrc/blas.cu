@@ -108,6 +108,27 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf
     set_conditions(ctl, S->trips < S->maxiter + 4 ? 1u : 0u, 0u);
 }
 
+// p_new = r + beta p_old, buffers by iteration parity
+template <typename R>
+__global__ void __launch_bounds__(kBlock)
+update_p_kernel(int vh, const R *__restrict__ r, R *pbuf0, R *pbuf1, const CgScalars *S) {
+    if (S->halt) return;
+    const int it = S->iters;
+    const R *pold = (it & 1) ? pbuf1 : pbuf0;
+    R *pnew = (it & 1) ? pbuf0 : pbuf1;
+    const R beta = (R)S->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
+        const Vec3<R> rv = load_vec(r, vh, i), pv = load_vec(pold, vh, i);
+        Vec3<R> o;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+            o.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+        }
+        store_vec(pnew, vh, i, o);
+    }
+}
+
 // x64 += xh32; xh32 = 0
 __global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restrict__ x, float *__restrict__ xh) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
@@ -220,6 +241,17 @@ qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, v
                                                        (float *)pbuf[1], (const float *)ap, S, lat->partials,
                                                        lat->counter, ctl);
     QEX_CHECK_LAUNCH("update_xr_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *const pbuf[2], CgScalars *S,
+                           cudaStream_t st) {
+    int nb = blas_blocks(lat), vh = (int)lat->vh;
+    if (prec == QEX_F64)
+        update_p_kernel<double><<<nb, kBlock, 0, st>>>(vh, (const double *)r, (double *)pbuf[0], (double *)pbuf[1], S);
+    else
+        update_p_kernel<float><<<nb, kBlock, 0, st>>>(vh, (const float *)r, (float *)pbuf[0], (float *)pbuf[1], S);
+    QEX_CHECK_LAUNCH("update_p_kernel");
     return QEX_OK;
 }
 

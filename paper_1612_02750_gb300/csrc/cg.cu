@@ -1,10 +1,11 @@
 // cg.cu -- conjugate gradient on A = m^2 - D_eo D_oe (even sites): plain FP64
 // and mixed precision with reliable updates.
 //
-// One iteration is three kernels and reads nothing back:
+// One iteration is three kernels (mixed precision) and reads nothing back:
 //   1. p_new = r + beta p_old formed on the fly at every neighbour read,
 //      tmp = D_oe p_new, and p_new stored (two p buffers, chosen by the parity
-//      of the device-side iteration count);
+//      of the device-side iteration count; FP64 CG forms p_new in a separate
+//      pass, because its Dslash is FP64-ALU bound);
 //   2. A p_new = m^2 p_new - D_eo tmp with <p_new, A p_new> -> alpha;
 //   3. x += alpha p_new, r -= alpha A p_new, ||r||^2 -> beta or a halt flag.
 // alpha, beta and the norms stay in device memory.  By default the whole
@@ -99,16 +100,26 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
     qex_status err;
     a.out_parity = 1;
     a.out = tmp;
-    a.epi = EPI_PUPD;
     a.r = r;
     a.pbuf[0] = pb[0];
     a.pbuf[1] = pb[1];
+    if (s.mixed) {
+        // FP32: the direction update rides along the first Dslash (its few
+        // extra FMAs per neighbour are free in a memory-bound kernel)
+        a.epi = EPI_PUPD;
+    } else {
+        // FP64: the Dslash is FP64-ALU bound, so the update is its own
+        // memory-bound pass instead of eight recomputations per site
+        if ((err = launch_update_p(lat, a.prec, r, pb, S, st))) return err;
+        a.epi = EPI_PLAIN;
+        a.psel = 1;
+    }
     if ((err = launch_dslash(lat, a, st))) return err;
     a.out_parity = 0;
     a.in = tmp;
     a.out = ap;
     a.epi = EPI_NORMAL;
-    a.qsel = 1;
+    a.psel = 1;
     a.m2 = s.m2;
     if ((err = launch_dslash(lat, a, st))) return err;
     return launch_update_xr(lat, a.prec, x, r, pb, ap, S, ctl, st);
@@ -196,7 +207,7 @@ static qex_status build_graph(Solve &s, CgGraph **out) {
     G->b64 = s.b64;
     G->x64 = s.x64;
     G->work = s.lat->work;
-    G->kernels_per_trip = 3;
+    G->kernels_per_trip = s.mixed ? 3 : 4;
     G->kernels_per_ru = s.mixed ? 4 : 3;
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaSuccess;

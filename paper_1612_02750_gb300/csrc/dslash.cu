@@ -40,7 +40,7 @@ struct DsParams {
     int check_halt;
     const R *r;         // EPI_PUPD
     R *pbuf0, *pbuf1;   // p ping-pong
-    int qsel;
+    int psel;
     double *partials;
     unsigned int *counter;
 };
@@ -48,7 +48,8 @@ struct DsParams {
 // Input colour vector at index j: the field itself, or (EPI_PUPD) the new
 // search direction r + beta p_old formed on the fly.
 template <typename R, int EPI>
-__device__ __forceinline__ Vec3<R> load_in(const DsParams<R> &P, size_t vh, int j, const R *pold, R beta) {
+__device__ __forceinline__ Vec3<R> load_in(const DsParams<R> &P, const R *in, size_t vh, int j, const R *pold,
+                                           R beta) {
     if constexpr (EPI == EPI_PUPD) {
         const Vec3<R> rv = load_vec(P.r, vh, j), pv = load_vec(pold, vh, j);
         Vec3<R> v;
@@ -59,12 +60,12 @@ __device__ __forceinline__ Vec3<R> load_in(const DsParams<R> &P, size_t vh, int 
         }
         return v;
     } else {
-        return load_vec(P.in, vh, j);
+        return load_vec(in, vh, j);
     }
 }
 
 template <typename R, int FMT, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kBlock) dslash_kernel(const DsParams<R> P) {
+__global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(const DsParams<R> P) {
     __shared__ double smem[32];
     __shared__ unsigned int is_last;
     if (P.check_halt && P.S->halt) return;  // uniform over the grid
@@ -77,6 +78,8 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(const DsParams<R> P) {
     const R *pold = nullptr;
     R *pnew = nullptr;
     R beta = R(0);
+    const R *in = P.in;
+    if (EPI == EPI_PLAIN && P.psel) in = (P.S->iters & 1) ? P.pbuf0 : P.pbuf1;  // the new direction
     if constexpr (EPI == EPI_PUPD) {
         const int it = P.S->iters;
         pold = (it & 1) ? P.pbuf1 : P.pbuf0;
@@ -95,13 +98,13 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(const DsParams<R> P) {
             {   // + eta b U_mu(x) psi(x + mu)
                 const int j = hop_index(g, s, mu, 1);
                 const Mat3<R> u = load_fat<R, FMT>(P.fat, vh, p, mu, i);
-                const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
+                const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
                 acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, v);
             }
             {   // - eta b U_mu(x - mu)^+ psi(x - mu)
                 const int j = hop_index(g, s, mu, -1);
                 const Mat3<R> u = load_fat<R, FMT>(P.fat, vh, 1 - p, mu, j);
-                const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
+                const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
                 acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, v);
             }
             if (NAIK) {
@@ -109,13 +112,13 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(const DsParams<R> P) {
                 {
                     const int j = hop_index(g, s, mu, 3);
                     const Mat3<R> u = load_link(P.lng, vh, p, mu, i);
-                    const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
+                    const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
                     acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, v);
                 }
                 {
                     const int j = hop_index(g, s, mu, -3);
                     const Mat3<R> u = load_link(P.lng, vh, 1 - p, mu, j);
-                    const Vec3<R> v = load_in<R, EPI>(P, vh, j, pold, beta);
+                    const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
                     acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, v);
                 }
             }
@@ -125,11 +128,11 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(const DsParams<R> P) {
         } else if constexpr (EPI == EPI_PUPD) {
             store_vec(P.out, vh, i, acc);
             // this thread also owns index i of the other parity's direction
-            store_vec(pnew, vh, i, load_in<R, EPI>(P, vh, i, pold, beta));
+            store_vec(pnew, vh, i, load_in<R, EPI>(P, in, vh, i, pold, beta));
         } else if constexpr (EPI == EPI_NORMAL) {
             // out = m^2 q - D in;  part = Re <q, out>
             const R *q = P.q;
-            if (P.qsel) q = (P.S->iters & 1) ? P.pbuf0 : P.pbuf1;  // the new direction
+            if (P.psel) q = (P.S->iters & 1) ? P.pbuf0 : P.pbuf1;  // the new direction
             const Vec3<R> qv = load_vec(q, vh, i);
             Vec3<R> o;
             R d = R(0);
@@ -225,10 +228,10 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.r = (const R *)a.r;
     P.pbuf0 = (R *)a.pbuf[0];
     P.pbuf1 = (R *)a.pbuf[1];
-    P.qsel = a.qsel;
+    P.psel = a.psel;
     P.partials = lat->partials;
     P.counter = lat->counter;
-    dslash_kernel<R, FMT, NAIK, EPI><<<blocks_for(lat->vh), kBlock, 0, st>>>(P);
+    dslash_kernel<R, FMT, NAIK, EPI><<<blocks_for(lat->vh, kDslashBlock), kDslashBlock, 0, st>>>(P);
 }
 
 template <typename R, int FMT, bool NAIK>

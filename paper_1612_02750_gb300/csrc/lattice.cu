@@ -80,7 +80,7 @@ int blas_blocks(const qex_lattice *lat) {
 // and the CG scalars with their pinned host mirror.
 qex_status ensure_scratch(qex_lattice *lat) {
     if (lat->partials) return QEX_OK;
-    int nb = blocks_for(lat->vh);
+    int nb = blocks_for(lat->vh, kDslashBlock < kBlock ? kDslashBlock : kBlock);
     int nbb = blas_blocks(lat);
     lat->partials_len = 2 * (nb > nbb ? nb : nbb);
     QEX_CUDA(cudaMalloc(&lat->partials, sizeof(double) * lat->partials_len));

@@ -353,6 +353,17 @@ inline bool is_f64(qex_prec p) { return p == QEX_F64; }
 
 constexpr int kBlock = 256;  // threads per block of the site kernels
 
+// Dslash launch shape: threads per block and the minimum resident blocks per
+// SM handed to __launch_bounds__ (which caps registers per thread).
+#ifndef QEX_DSLASH_BLOCK
+#define QEX_DSLASH_BLOCK 256
+#endif
+#ifndef QEX_DSLASH_MIN_BLOCKS
+#define QEX_DSLASH_MIN_BLOCKS 3
+#endif
+constexpr int kDslashBlock = QEX_DSLASH_BLOCK;
+constexpr int kDslashMinBlocks = QEX_DSLASH_MIN_BLOCKS;
+
 inline int blocks_for(int64_t n, int bs = kBlock) { return (int)((n + bs - 1) / bs); }
 
 }  // namespace qex

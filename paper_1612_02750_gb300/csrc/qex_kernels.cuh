@@ -55,15 +55,15 @@ struct DslashArgs {
     const void *in;      // EPI_PLAIN / NORMAL / RESID
     void *out;
     int epi;
-    const void *q;       // EPI_NORMAL / EPI_RESID (ignored when qsel)
+    const void *q;       // EPI_NORMAL / EPI_RESID (ignored when psel)
     const double *b;     // EPI_RESID (FP64 half field)
     double m2;
     CgScalars *S;        // EPI_NORMAL / EPI_RESID / halt check / buffer selection
     int check_halt;
     // CG direction ping-pong: p_old = pbuf[iters & 1], p_new = pbuf[(iters + 1) & 1]
     const void *r;       // EPI_PUPD
-    void *pbuf[2];       // EPI_PUPD, and EPI_NORMAL when qsel
-    int qsel;            // EPI_NORMAL: q = p_new
+    void *pbuf[2];       // EPI_PUPD, and EPI_PLAIN / EPI_NORMAL when psel
+    int psel;            // EPI_PLAIN: in = p_new; EPI_NORMAL: q = p_new
 };
 
 qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
@@ -72,6 +72,10 @@ qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st)
 // graph conditions when ctl.active.
 qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, void *const pbuf[2],
                             const void *ap, CgScalars *S, const GraphCtl &ctl, cudaStream_t st);
+// p_new = r + beta p_old with the buffers chosen by the iteration parity
+// (halt-checked); the FP64 iteration's first kernel.
+qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *const pbuf[2], CgScalars *S,
+                           cudaStream_t st);
 // x64 += (double) xh32; xh32 = 0.
 qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st);
 // r32 = (float) r64 (r32 may be NULL: only the graph condition is set);
