@@ -72,7 +72,6 @@ __global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(
 
     const Geom &g = P.g;
     const size_t vh = (size_t)g.vh;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = P.p;
     // direction buffers by iteration parity (read before any block can change it)
     const R *pold = nullptr;
@@ -87,7 +86,9 @@ __global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(
         beta = (R)P.S->beta;
     }
     double part = 0.0;
-    if (i < g.vh) {
+    // grid-stride over the sites: one pass per thread when the grid covers
+    // the lattice, several when the launch is persistent (reducing variants)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += gridDim.x * blockDim.x) {
         const Site s = site_of(g, p, i);
         Vec3<R> acc;
 #pragma unroll
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(
                 d = fma(qv.c[a].im, o.c[a].im, d);
             }
             store_vec(P.out, vh, i, o);
-            part = (double)d;
+            part += (double)d;
         } else {
             // out = b - m^2 q + D in;  part = ||out||^2   (FP64 only)
             const Vec3<R> qv = load_vec(P.q, vh, i);
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(
                 d = fma((double)o.c[a].im, (double)o.c[a].im, d);
             }
             store_vec(P.out, vh, i, o);
-            part = d;
+            part += d;
         }
     }
     if constexpr (EPI == EPI_PLAIN || EPI == EPI_PUPD) {
@@ -210,6 +211,16 @@ __global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(
     }
 }
 
+// Grid of a Dslash launch: one thread per site, or, for the variants that end
+// in a grid reduction, a persistent grid of kDslashMinBlocks blocks per SM so
+// that each block pays the reduction's fence-and-atomic tail once.
+static int dslash_grid(const qex_lattice *lat, bool reducing) {
+    const int full = blocks_for(lat->vh, kDslashBlock);
+    if (!reducing) return full;
+    const int persistent = sm_count() * kDslashMinBlocks;
+    return full < persistent ? full : persistent;
+}
+
 template <typename R, int FMT, bool NAIK, int EPI>
 static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     DsParams<R> P;
@@ -231,7 +242,8 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.psel = a.psel;
     P.partials = lat->partials;
     P.counter = lat->counter;
-    dslash_kernel<R, FMT, NAIK, EPI><<<blocks_for(lat->vh, kDslashBlock), kDslashBlock, 0, st>>>(P);
+    dslash_kernel<R, FMT, NAIK, EPI><<<dslash_grid(lat, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr),
+                                       kDslashBlock, 0, st>>>(P);
 }
 
 template <typename R, int FMT, bool NAIK>

@@ -62,7 +62,7 @@ qex_status check_prec(qex_prec prec) {
     return QEX_OK;
 }
 
-int blas_blocks(const qex_lattice *lat) {
+int sm_count() {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0, n = 0;
@@ -70,8 +70,12 @@ int blas_blocks(const qex_lattice *lat) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
         sms = n;
     }
+    return sms;
+}
+
+int blas_blocks(const qex_lattice *lat) {
     int want = blocks_for(lat->vh);
-    int cap = sms * 8;
+    int cap = sm_count() * 8;
     return want < cap ? want : cap;
 }
 

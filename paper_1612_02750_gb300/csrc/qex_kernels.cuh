@@ -90,6 +90,7 @@ qex_status launch_dot(qex_lattice *lat, qex_prec prec, const void *a, const void
                       cudaStream_t st);
 
 int blas_blocks(const qex_lattice *lat);
+int sm_count();
 void note_launches(unsigned long long n);
 void set_count_launches(bool on);
 void free_cg_graph(void *g);
