@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="Dslash bandwidth sweep over L^3 x T volumes (and 48^4, 64^4), with and without the Naik "
+                         "term, in every precision: one JSON line per case")
+    ap.add_argument("--sweep-cg", action="store_true",
+                    help="with --sweep: also the mixed-precision CG of the 64^4 Naik workload")
     ap.add_argument("--dslash-only", action="store_true",
                     help="profiling case: two launches each of the two-row FP32, FP32 and FP64 one-hop Dslash "
                          "on the workload, no timing")
@@ -431,9 +436,82 @@ def run_dslash_only():
     print("dslash-only done", float(out.abs().sum()))
 
 
+SWEEP_L = (8, 12, 16, 24, 32)
+SWEEP_T = (8, 12, 16, 24, 32, 48, 64)
+BYTES_NAIK = {"f64": 2400, "f32": 1200, "f32r12": 1008}  # 16 links (8 two-row fat) + 16 in once + 1 out
+FLOP_NAIK = 1146
+
+
+def run_sweep(args):
+    """Dslash timing over the paper's L^3 x T volume grid plus 48^4 and 64^4.
+    Links and fields are random device tensors (timing only; parity is tested
+    elsewhere); each case is 5 warm-up and 30 timed launches on one stream."""
+    import torch
+
+    import paper_1612_02750_gb300 as q
+    from paper_1612_02750_gb300 import build as qbuild
+
+    qbuild.build()
+    q.load()
+    peak, peak_kind = measured_peak()
+    shapes = [(L, L, L, T) for L in SWEEP_L for T in SWEEP_T] + [(48, 48, 48, 48), (64, 64, 64, 64)]
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    for dims in shapes:
+        lat = q.Lattice(dims)
+        vh = lat.half_volume
+        fat64 = torch.randn(q.qex_links_bytes(lat, "f64") // 8, dtype=torch.float64, device="cuda", generator=gen)
+        lng64 = torch.randn_like(fat64)
+        sets = {"f64": (fat64, lng64), "f32": (fat64.float(), lng64.float())}
+        sets["f32r12"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12"), sets["f32"][1])
+        for prec, (fat, lng) in sets.items():
+            inp = q.empty_field(lat, prec).normal_(generator=gen)
+            out = q.empty_field(lat, prec)
+            for naik in (False, True):
+                lg = lng if naik else None
+                for _ in range(5):
+                    q.qex_dslash(lat, prec, fat, lg, -1.0 / 24, 1, inp, out)
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(30):
+                    q.qex_dslash(lat, prec, fat, lg, -1.0 / 24, 1, inp, out)
+                z.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(z) / 30
+                nbytes = (BYTES_NAIK if naik else BYTES_NN)[prec] * vh
+                flops = (FLOP_NAIK if naik else FLOP_NN) * vh
+                gbs = nbytes / (ms * 1e-3) / 1e9
+                print(json.dumps({"sweep": "dslash", "lattice": list(dims), "naik": naik, "prec": prec,
+                                  "us": round(ms * 1e3, 2), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                  "GFLOP/s": round(flops / (ms * 1e-3) / 1e9, 1),
+                                  "l2_resident": nbytes < L2_BYTES, "peak": f"{peak_kind} {peak}"}), flush=True)
+        del sets, fat64, lng64, fat, lng, inp, out
+        lat.close()
+        torch.cuda.empty_cache()
+    if args.sweep_cg:
+        import fieldgen as fg
+
+        wl = fg.workload("cfg64naik")
+        u, w, b = fg.make_inputs_sliced(wl["dims"], wl["fat"], True, wl["seed"])
+        lat = q.Lattice(wl["dims"])
+        fat64 = q.qex_pack_links(lat, "f64", torch.from_numpy(u).cuda())
+        lng64 = q.qex_pack_links(lat, "f64", torch.from_numpy(w).cuda())
+        del u, w
+        torch.cuda.empty_cache()
+        fatr = q.qex_convert_links(lat, "f64", fat64, "f32r12")
+        lng32 = q.qex_convert_links(lat, "f64", lng64, "f32")
+        bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
+        x = torch.zeros_like(bh)
+        st, stats = q.qex_cg(lat, "f32r12", fat64, lng64, fatr, lng32, -1.0 / 24, wl["mass"], bh, x, tol=TOL,
+                             maxiter=60000, delta=DELTA, check=False)
+        print(json.dumps({"sweep": "cg", "workload": "64^4 Naik, Haar fat links, Gaussian/sqrt(3) long links, "
+                          "c3=-1/24, m=0.005", "status": st, **stats}), flush=True)
+
+
 def main():
     args = parse()
-    if args.dslash_only:
+    if args.sweep:
+        run_sweep(args)
+    elif args.dslash_only:
         run_dslash_only()
     elif args.impl == "reference":
         run_reference(args)

@@ -132,15 +132,20 @@ def random_links(dims, kind: str, rng, a: float = 0.3) -> np.ndarray:
     ``haar``: Haar SU(3); ``exp``: exp(i a H); ``gauss3``: complex Gaussian
     entries / sqrt(3) (non-unitary long links); ``unit``: identity links.
     """
-    shape = lattice_shape(dims) + (4,)
+    return _draw_links(lattice_shape(dims) + (4,), kind, rng, a)
+
+
+def _draw_links(shape, kind: str, rng, a: float) -> np.ndarray:
+    if kind == "unit":
+        out = np.zeros(tuple(shape) + (3, 3), dtype=np.complex128)
+        out[...] = np.eye(3)
+        return out
     if kind == "haar":
         return haar_su3(rng, shape)
     if kind == "exp":
         return exp_i_su3(rng, shape, a)
     if kind == "gauss3":
-        return complex_gaussian(rng, shape + (3, 3), 1.0 / np.sqrt(3.0))
-    if kind == "unit":
-        return unit_links(dims)
+        return complex_gaussian(rng, tuple(shape) + (3, 3), 1.0 / np.sqrt(3.0))
     raise ValueError(f"unknown link kind {kind!r}")
 
 
@@ -177,5 +182,25 @@ def make_inputs(dims, fat: str = "haar", naik: bool = False, seed: int = 1, a: f
     u = random_links(dims, fat, s["links"], a)
     w = random_links(dims, "gauss3", s["long_links"]) if naik else None
     b = gaussian_field(s["source"], dims)
+    b[~even_mask(dims)] = 0
+    return u, w, b
+
+
+def make_inputs_sliced(dims, fat: str = "haar", naik: bool = False, seed: int = 1, a: float = 0.3):
+    """As :func:`make_inputs`, but every input is drawn one t-slice at a time
+    (bounded temporary host memory for large lattices such as 64^4).  The
+    values differ from :func:`make_inputs`' for the same seed."""
+    s = rng_streams(seed)
+    shp = lattice_shape(dims)
+    u = np.empty(shp + (4, 3, 3), dtype=np.complex128)
+    w = np.empty(shp + (4, 3, 3), dtype=np.complex128) if naik else None
+    sl = (1,) + shp[1:] + (4,)
+    for t in range(shp[0]):
+        u[t] = _draw_links(sl, fat, s["links"], a)[0]
+        if naik:
+            w[t] = _draw_links(sl, "gauss3", s["long_links"], a)[0]
+    b = np.empty(shp + (3,), dtype=np.complex128)
+    for t in range(shp[0]):
+        b[t] = complex_gaussian(s["source"], (1,) + shp[1:] + (3,))[0]
     b[~even_mask(dims)] = 0
     return u, w, b

@@ -145,37 +145,56 @@ static void add_mdagv(cplx acc[3], double s, const cplx *M, const cplx *v) {
 
 /* ------------------------------------------------------------------ operator */
 
-/* out = D in on the full lattice (formula in the header).  W may be NULL (no
- * Naik term).  `in` and `out` must not alias. */
+/* acc = (D in)(x) at the site of lexicographic index s (formula in the
+ * header).  W may be NULL (no Naik term). */
+static void dslash_at(const int L[4], int antiperiodic, const cplx *U, const cplx *W, double c3,
+                      const cplx *in, int64_t s, cplx acc[3]) {
+    int x[4], y[4];
+    oracle_coords(L, s, x);
+    acc[0] = acc[1] = acc[2] = 0;
+    for (int mu = 0; mu < 4; ++mu) {
+        /* forward one-hop: eta_mu(x) b U_mu(x) psi(x+mu) */
+        shifted(L, x, mu, +1, y);
+        add_mv(acc, oracle_eta(mu, x) * oracle_link_bc(L, antiperiodic, mu, x, 1),
+               link_at(U, s, mu), in + 3 * oracle_lex(L, y));
+        /* backward one-hop: -eta_mu(y) b U_mu(y)^+ psi(y), y = x - mu */
+        shifted(L, x, mu, -1, y);
+        int64_t ly = oracle_lex(L, y);
+        add_mdagv(acc, -oracle_eta(mu, y) * oracle_link_bc(L, antiperiodic, mu, y, 1),
+                  link_at(U, ly, mu), in + 3 * ly);
+        if (W) {
+            shifted(L, x, mu, +3, y);
+            add_mv(acc, c3 * oracle_eta(mu, x) * oracle_link_bc(L, antiperiodic, mu, x, 3),
+                   link_at(W, s, mu), in + 3 * oracle_lex(L, y));
+            shifted(L, x, mu, -3, y);
+            ly = oracle_lex(L, y);
+            add_mdagv(acc, -c3 * oracle_eta(mu, y) * oracle_link_bc(L, antiperiodic, mu, y, 3),
+                      link_at(W, ly, mu), in + 3 * ly);
+        }
+    }
+}
+
+/* out = D in on the full lattice.  `in` and `out` must not alias. */
 void oracle_dslash(const int L[4], int antiperiodic, const cplx *U, const cplx *W, double c3,
                    const cplx *in, cplx *out) {
     int64_t V = oracle_volume(L);
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < V; ++s) {
-        int x[4], y[4];
-        oracle_coords(L, s, x);
-        cplx acc[3] = {0, 0, 0};
-        for (int mu = 0; mu < 4; ++mu) {
-            /* forward one-hop: eta_mu(x) b U_mu(x) psi(x+mu) */
-            shifted(L, x, mu, +1, y);
-            add_mv(acc, oracle_eta(mu, x) * oracle_link_bc(L, antiperiodic, mu, x, 1),
-                   link_at(U, s, mu), in + 3 * oracle_lex(L, y));
-            /* backward one-hop: -eta_mu(y) b U_mu(y)^+ psi(y), y = x - mu */
-            shifted(L, x, mu, -1, y);
-            int64_t ly = oracle_lex(L, y);
-            add_mdagv(acc, -oracle_eta(mu, y) * oracle_link_bc(L, antiperiodic, mu, y, 1),
-                      link_at(U, ly, mu), in + 3 * ly);
-            if (W) {
-                shifted(L, x, mu, +3, y);
-                add_mv(acc, c3 * oracle_eta(mu, x) * oracle_link_bc(L, antiperiodic, mu, x, 3),
-                       link_at(W, s, mu), in + 3 * oracle_lex(L, y));
-                shifted(L, x, mu, -3, y);
-                ly = oracle_lex(L, y);
-                add_mdagv(acc, -c3 * oracle_eta(mu, y) * oracle_link_bc(L, antiperiodic, mu, y, 3),
-                          link_at(W, ly, mu), in + 3 * ly);
-            }
-        }
+        cplx acc[3];
+        dslash_at(L, antiperiodic, U, W, c3, in, s, acc);
         for (int a = 0; a < 3; ++a) out[3 * s + a] = acc[a];
+    }
+}
+
+/* out[3k..3k+2] = (D in)(x_k) for the n sites of lexicographic index
+ * sites[k] (the same sum as oracle_dslash, evaluated only there). */
+void oracle_dslash_sites(const int L[4], int antiperiodic, const cplx *U, const cplx *W, double c3,
+                         const cplx *in, const int64_t *sites, int64_t n, cplx *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        cplx acc[3];
+        dslash_at(L, antiperiodic, U, W, c3, in, sites[k], acc);
+        for (int a = 0; a < 3; ++a) out[3 * k + a] = acc[a];
     }
 }
 

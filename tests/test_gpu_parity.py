@@ -336,3 +336,46 @@ def test_full_size_32_dslash_and_mixed_cg(q, oracle_mod):
     xf = host(q.qex_unpack_field(lat, "f64", 0, x))
     tr = oracle_mod.true_residual(dims, u, b, xf, wl["mass"])
     assert st == 0 and tr <= 1.05e-10, (stats, tr)
+
+
+@pytest.mark.slow
+def test_full_size_64_naik_sampled_sites(q, oracle_mod):
+    """The 64^4 workload with the Naik term (Haar fat links, Gaussian/sqrt(3)
+    long links, c3 = -1/24) in the launch configuration the sweep times:
+    both parities and all three precisions on 4096 sampled output sites
+    against the oracle's per-site sum, and anti-hermiticity
+    <chi, D_eo psi> = -<D_oe chi, psi> over the whole lattice in FP64."""
+    import torch
+
+    wl = fg.workload("cfg64naik")
+    dims = wl["dims"]
+    u, w, b = fg.make_inputs_sliced(dims, wl["fat"], True, wl["seed"])
+    psi = fg.gaussian_field(fg.rng_streams(wl["seed"] + 100)["source"], dims)
+    lat = q.Lattice(dims)
+    fat64 = q.qex_pack_links(lat, "f64", dev(u))
+    lng64 = q.qex_pack_links(lat, "f64", dev(w))
+    torch.cuda.empty_cache()
+    links = {"f64": (fat64, lng64),
+             "f32": (q.qex_convert_links(lat, "f64", fat64, "f32"), q.qex_convert_links(lat, "f64", lng64, "f32"))}
+    links["f32r12"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12"), links["f32"][1])
+    rng = np.random.default_rng(17)
+    ev = fg.even_mask(dims).reshape(-1)
+    psi_d = dev(psi)
+    for out_p in (0, 1):
+        cand = np.flatnonzero(ev if out_p == 0 else ~ev)
+        sites = np.sort(rng.choice(cand, 4096, replace=False))
+        ref = oracle_mod.dslash_sites(dims, u, psi, sites, w, C3, True)
+        for prec, (fat, lng) in links.items():
+            inp = q.qex_pack_field(lat, prec, 1 - out_p, psi_d)
+            out = q.qex_dslash(lat, prec, fat, lng, C3, out_p, inp)
+            full = q.qex_unpack_field(lat, prec, out_p, out).reshape(-1, 3)
+            got = full[torch.from_numpy(sites).cuda()].cpu().numpy()
+            assert relerr(got, ref) <= TOL[prec], (out_p, prec)
+            del out, full
+    chi_e = q.qex_pack_field(lat, "f64", 0, dev(b))
+    psi_o = q.qex_pack_field(lat, "f64", 1, psi_d)
+    d_eo_psi = q.qex_dslash(lat, "f64", fat64, lng64, C3, 0, psi_o)
+    d_oe_chi = q.qex_dslash(lat, "f64", fat64, lng64, C3, 1, chi_e)
+    lhs = host(q.qex_dot(lat, "f64", chi_e, d_eo_psi))
+    rhs = host(q.qex_dot(lat, "f64", d_oe_chi, psi_o))
+    assert abs(complex(*lhs) + complex(*rhs)) <= 1e-12 * abs(complex(*lhs))

@@ -103,6 +103,19 @@ def test_antihermitian(oracle_mod, dims, naik, antiperiodic):
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
 
 
+def test_dslash_at_sampled_sites_equals_full_lattice(oracle_mod):
+    """The sampled-site evaluation is the full-lattice sum restricted to the
+    listed sites (bit-identical)."""
+    dims = (8, 4, 6, 8)
+    s = fg.rng_streams(14)
+    u = _rand_links(s["links"], dims)
+    w = _rand_links(s["long_links"], dims)
+    psi = fg.gaussian_field(s["source"], dims)
+    full = oracle_mod.dslash(dims, u, psi, w, C3, True).reshape(-1, 3)
+    sites = np.array([0, 1, 7, 100, 767, 1535, 900], dtype=np.int64)
+    assert np.array_equal(oracle_mod.dslash_sites(dims, u, psi, sites, w, C3, True), full[sites])
+
+
 @pytest.mark.parametrize("naik", [False, True])
 def test_gauge_covariance(oracle_mod, naik):
     """U_mu(x) -> g(x) U_mu(x) g(x+mu)^+, W_mu(x) -> g(x) W_mu(x) g(x+3mu)^+,
