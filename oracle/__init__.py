@@ -63,6 +63,7 @@ def _load():
         lib.oracle_cg.restype = ctypes.c_int
         lib.oracle_cg.argtypes = [i4, ctypes.c_int, vp, vp, d, d, vp, vp, d, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_force.argtypes = [i4, ctypes.c_int, vp, vp, d, vp, vp, ctypes.c_int, vp, vp]
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -200,6 +201,40 @@ def cg(dims, u, b, mass: float, w=None, c3: float = 0.0, tol: float = 1e-10, max
     rc = _load().oracle_cg(L, int(antiperiodic), _ptr(u), _ptr(w), float(c3), float(mass), _ptr(b),
                            _ptr(x), float(tol), int(maxiter), ctypes.byref(it), ctypes.byref(tr))
     return x, rc == 0, int(it.value), float(tr.value)
+
+
+def force(dims, u, x_even, y_odd, w=None, c3: float = 0.0, kind: int = 0, antiperiodic: bool = True):
+    """Per-link force of S = phi^+ A^{-1} phi from X = A^{-1} phi (even sites)
+    and Y = D_oe X (odd sites): kind 0 gives F = 2 TA(U G), kind 1 gives 2 G^+
+    (the gradient of the real S with respect to the complex link entries).
+    Returns (F_fat, F_long or None) in the links layout."""
+    L = _dims(dims)
+    u = _clinks(u, dims)
+    w = _clinks(w, dims)
+    x = _cfield(x_even, dims)
+    y = _cfield(y_odd, dims)
+    ff = np.empty_like(u)
+    fl = np.empty_like(w) if w is not None else None
+    _load().oracle_force(L, int(antiperiodic), _ptr(u), _ptr(w), float(c3), _ptr(x), _ptr(y), int(kind), _ptr(ff),
+                         _ptr(fl))
+    return ff, fl
+
+
+def pseudofermion(dims, u, chi, mass: float, w=None, c3: float = 0.0, antiperiodic: bool = True):
+    """phi = (M^+ chi) on even sites, M = m + D: phi_e = m chi_e - D_eo chi_o."""
+    ev = even_sites(dims)
+    dch = dslash_parity(dims, u, chi, 0, w, c3, antiperiodic)
+    phi = mass * chi - dch
+    phi[~ev] = 0
+    return phi
+
+
+def action(dims, u, phi, mass: float, w=None, c3: float = 0.0, tol: float = 1e-13, antiperiodic: bool = True):
+    """S = Re phi^+ A^{-1} phi by the oracle's CG; returns (S, X)."""
+    x, ok, _, _ = cg(dims, u, phi, mass, w, c3, tol=tol, maxiter=200000, antiperiodic=antiperiodic)
+    if not ok:
+        raise RuntimeError("oracle CG did not converge")
+    return float(np.vdot(phi, x).real), x
 
 
 # ----------------------------------------------------------------- numpy helpers

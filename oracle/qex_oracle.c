@@ -332,6 +332,76 @@ int oracle_cg(const int L[4], int antiperiodic, const cplx *U, const cplx *W, do
     return converged ? 0 : 1;
 }
 
+/* ------------------------------------------------------------------ force */
+
+/* Fermion force of S = phi^+ A^{-1} phi (A = m^2 - D_eo D_oe on even sites).
+ * With X = A^{-1} phi on even sites and Y = D_oe X on odd sites,
+ * dS = -X^+ dA X = 2 Re X^+ dD_eo Y = 2 Re sum_{x,mu} tr(dU_mu(x) G_mu(x)):
+ * D is anti-Hermitian for any links, so X^+ D_eo = -(D_oe X)^+ and
+ * dD_oe = -dD_eo^+.  Collecting the terms of dD_eo link by link:
+ *   G_mu(x) =  s_mu(x) Y(x+mu) X(x)^+    for even x,
+ *   G_mu(x) = -s_mu(x) X(x+mu) Y(x)^+    for odd x,
+ * with s_mu the staggered phase times the boundary sign of that link, and
+ * the same with c3 and the 3-hop neighbours for the long links.  Outputs,
+ * per link (links layout, full lattice):
+ *   kind 0:  F = 2 TA(U G), TA(M) = (M - M^+)/2 - tr(M - M^+)/6 (traceless
+ *            anti-Hermitian part): dS/de along U -> exp(i e w) U is
+ *            sum i tr(w F) for Hermitian traceless w;
+ *   kind 1:  2 G^+ = 2 dS/d(conj U): for any complex dU,
+ *            dS = Re sum conj(2 G^+)_ab dU_ab (the gradient convention of
+ *            torch for a real loss of complex inputs).
+ * X and Y are full-lattice fields (X on even sites, Y on odd sites; the
+ * other sites are ignored).  W and out_long may be NULL. */
+static void force_links(const int L[4], int antiperiodic, const cplx *U, double coef, int hop, const cplx *X,
+                        const cplx *Y, int kind, cplx *out) {
+    int64_t V = oracle_volume(L);
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < V; ++s) {
+        int x[4], y[4];
+        oracle_coords(L, s, x);
+        int even = oracle_parity(x) == 0;
+        for (int mu = 0; mu < 4; ++mu) {
+            shifted(L, x, mu, hop, y);
+            int64_t ly = oracle_lex(L, y);
+            double sgn = coef * oracle_eta(mu, x) * oracle_link_bc(L, antiperiodic, mu, x, hop);
+            const cplx *a = even ? Y + 3 * ly : X + 3 * ly;   /* field at x + hop mu */
+            const cplx *b = even ? X + 3 * s : Y + 3 * s;     /* field at x */
+            if (!even) sgn = -sgn;
+            cplx G[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) G[3 * i + j] = sgn * a[i] * conj(b[j]);
+            cplx *o = out + (s * 4 + mu) * 9;
+            if (kind == 1) {
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) o[3 * i + j] = 2.0 * conj(G[3 * j + i]);
+                continue;
+            }
+            const cplx *u = link_at(U, s, mu);
+            cplx M[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    cplx t = 0;
+                    for (int k = 0; k < 3; ++k) t += u[3 * i + k] * G[3 * k + j];
+                    M[3 * i + j] = t;
+                }
+            cplx tr = 0;
+            for (int i = 0; i < 3; ++i) tr += M[4 * i] - conj(M[4 * i]);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    cplx ta = 0.5 * (M[3 * i + j] - conj(M[3 * j + i]));
+                    if (i == j) ta -= tr / 6.0;
+                    o[3 * i + j] = 2.0 * ta;
+                }
+        }
+    }
+}
+
+void oracle_force(const int L[4], int antiperiodic, const cplx *U, const cplx *W, double c3, const cplx *X,
+                  const cplx *Y, int kind, cplx *out_fat, cplx *out_long) {
+    force_links(L, antiperiodic, U, 1.0, 1, X, Y, kind, out_fat);
+    if (W && out_long) force_links(L, antiperiodic, W, c3, 3, X, Y, kind, out_long);
+}
+
 /* Number of OpenMP threads the site loops use (1 without OpenMP). */
 int oracle_threads(void) {
 #ifdef _OPENMP
