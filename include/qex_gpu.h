@@ -230,6 +230,29 @@ qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, con
                   void *x64, double tol, int maxiter, double delta, void *stream,
                   qex_cg_stats *stats);
 
+/* ---------------------------------------------------------------- force */
+
+/* Fermion force of the pseudofermion action S = phi^+ A^{-1} phi,
+ * A = m^2 - D_eo D_oe on even sites (the paper, Sec. 4, lists hybrid Monte
+ * Carlo gauge generation, whose molecular dynamics needs this derivative).
+ * Inputs: x_even = X = A^{-1} phi (F64 even half field, e.g. from qex_cg) and
+ * y_odd = Y = D_oe X (F64 odd half field, e.g. from qex_dslash with
+ * out_parity 1).  Since D is anti-Hermitian for any links,
+ * dS = 2 Re sum_{x,mu} tr(dU_mu(x) G_mu(x)) with
+ *   G_mu(x) =  s_mu(x) Y(x+mu) X(x)^+  (x even),
+ *   G_mu(x) = -s_mu(x) X(x+mu) Y(x)^+  (x odd),
+ * s_mu the staggered phase times the link's antiperiodic sign; for the long
+ * links c_naik s3_mu and the x+3mu neighbours.  kind = 0 writes
+ * F = 2 TA(U G) per link (traceless anti-Hermitian: dS/de along
+ * U -> exp(i e w) U is sum i tr(w F)); kind = 1 writes 2 G^+, the gradient of
+ * the real S with respect to the complex link entries (dS = Re sum
+ * conj(2 G^+)_ab dU_ab).  out_fat (and out_lng when lng64 is given) receive
+ * one internal F64 link set each (qex_unpack_links converts them).
+ * Errors: QEX_ERR_ARG (NULL, bad kind), QEX_ERR_ALIGN, QEX_ERR_SHAPE (Naik on
+ * an extent < 4). */
+qex_status qex_force(const qex_lattice *lat, const void *fat64, const void *lng64, double c_naik,
+                     const void *x_even, const void *y_odd, int kind, void *out_fat, void *out_lng, void *stream);
+
 /* End-to-end solve from HOST memory (the call for users whose fields live
  * on the host).  host_fat (and host_lng, or NULL) are canonical complex-double
  * links [V][4][3][3]; host_b is a canonical complex-double field [V][3] whose

@@ -85,6 +85,7 @@ def load():
         "qex_dot": (i, [vp, i, vp, vp, vp, vp]),
         "qex_cg": (i, [vp, i, vp, vp, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_cg_host": (i, [vp, i, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_force": (i, [vp, vp, vp, d, vp, vp, i, vp, vp, vp]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -103,7 +104,7 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_launch_count", "qex_last_error", "qex_version"]
+            "qex_cg_host", "qex_force", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -333,6 +334,62 @@ def qex_cg(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, mass:
     if check:
         _check(st)
     return st, stats.as_dict()
+
+
+# -------------------------------------------------------------------- force
+
+def qex_force(lat: Lattice, fat64, lng64, c_naik: float, x_even, y_odd, kind: int = 0, out_fat=None, out_lng=None,
+              stream=None):
+    """Per-link force (kind 0: F = 2 TA(U G)) or gradient (kind 1: 2 G^+) of
+    S = phi^+ A^{-1} phi from X = A^{-1} phi and Y = D_oe X; internal F64
+    link sets.  Returns (out_fat, out_lng or None)."""
+    out_fat = empty_links(lat, "f64") if out_fat is None else out_fat
+    if lng64 is not None and out_lng is None:
+        out_lng = empty_links(lat, "f64")
+    _check(load().qex_force(lat.handle, _ptr(fat64), _ptr(lng64), float(c_naik), _ptr(x_even), _ptr(y_odd),
+                            int(kind), _ptr(out_fat), _ptr(out_lng) if lng64 is not None else None,
+                            _stream(stream)))
+    return out_fat, (out_lng if lng64 is not None else None)
+
+
+class StaggeredAction(torch.autograd.Function):
+    """S = Re phi^+ (m^2 - D_eo D_oe)^{-1} phi as a differentiable function of
+    the canonical complex128 links U (and long links W).
+
+    forward(U, W, phi, lat, mass, c_naik, inner, tol, delta): phi is a
+    canonical complex128 field whose even sites are the pseudofermion (held
+    fixed); inner = "f64" or a mixed precision ("f32", "f32r12").  The solve
+    is qex_cg; the backward pass is qex_dslash (Y = D_oe X) and qex_force
+    (kind 1), unpacked to canonical links: grad_U = 2 G^+ times the incoming
+    gradient (torch's convention for a real loss of complex inputs)."""
+
+    @staticmethod
+    def forward(ctx, U, W, phi, lat, mass, c_naik=0.0, inner="f64", tol=1e-12, delta=0.01):
+        fat64 = qex_pack_links(lat, "f64", U.detach().contiguous())
+        lng64 = qex_pack_links(lat, "f64", W.detach().contiguous()) if W is not None else None
+        fat32 = lng32 = None
+        if _prec(inner) != F64:
+            fat32 = qex_convert_links(lat, "f64", fat64, inner)
+            lng32 = qex_convert_links(lat, "f64", lng64, "f32") if lng64 is not None else None
+        b = qex_pack_field(lat, "f64", 0, phi.detach().contiguous())
+        x = torch.zeros_like(b)
+        qex_cg(lat, inner, fat64, lng64, fat32, lng32, c_naik, mass, b, x, tol=tol, delta=delta)
+        s = qex_dot(lat, "f64", b, x)[0]
+        ctx.lat, ctx.c_naik = lat, c_naik
+        ctx.has_w = W is not None
+        ctx.save_for_backward(fat64, lng64 if lng64 is not None else fat64, x)
+        return s.clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        fat64, lng64, x = ctx.saved_tensors
+        lat = ctx.lat
+        lng64 = lng64 if ctx.has_w else None
+        y = qex_dslash(lat, "f64", fat64, lng64, ctx.c_naik, 1, x)
+        gf, gl = qex_force(lat, fat64, lng64, ctx.c_naik, x, y, kind=1)
+        gU = qex_unpack_links(lat, "f64", gf) * grad_out
+        gW = qex_unpack_links(lat, "f64", gl) * grad_out if gl is not None else None
+        return gU, gW, None, None, None, None, None, None, None
 
 
 def _host_ptr(t, dtype):
