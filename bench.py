@@ -56,6 +56,9 @@ def parse():
                          "term, in every precision: one JSON line per case")
     ap.add_argument("--sweep-cg", action="store_true",
                     help="with --sweep: also the mixed-precision CG of the 64^4 Naik workload")
+    ap.add_argument("--mrhs", action="store_true",
+                    help="multi-RHS case: 24^4 Haar links, 16 Gaussian sources, batched Dslash and CG against "
+                         "single-RHS calls")
     ap.add_argument("--dslash-only", action="store_true",
                     help="profiling case: two launches each of the two-row FP32, FP32 and FP64 one-hop Dslash "
                          "on the workload, no timing")
@@ -507,9 +510,92 @@ def run_sweep(args):
                           "c3=-1/24, m=0.005", "status": st, **stats}), flush=True)
 
 
+MRHS_MASS = 0.05  # the 16-source solve's mass (the workload names masses only for the multi-lattice case)
+
+
+def run_mrhs(args):
+    """24^4, Haar links (seed 4), 16 Gaussian even-site sources: batched
+    two-row FP32 Dslash per right-hand side vs the single-RHS kernel, and the
+    batched mixed-precision solve vs 16 single-RHS solves of the same
+    sources."""
+    import torch
+
+    import fieldgen as fg
+    import paper_1612_02750_gb300 as q
+    from paper_1612_02750_gb300 import build as qbuild
+
+    qbuild.build()
+    q.load()
+    dims, nrhs, seed = (24, 24, 24, 24), 16, 4
+    st = fg.rng_streams(seed)
+    u = fg.random_links(dims, "haar", st["links"])
+    ev = fg.even_mask(dims)
+    srcs = []
+    for _ in range(nrhs):
+        b = fg.gaussian_field(st["source"], dims)
+        b[~ev] = 0
+        srcs.append(b)
+    lat = q.Lattice(dims)
+    vh = lat.half_volume
+    fat64 = q.qex_pack_links(lat, "f64", torch.from_numpy(u).cuda())
+    fatr = q.qex_convert_links(lat, "f64", fat64, "f32r12")
+    n64 = q.qex_field_bytes(lat, "f64") // 8
+    B = torch.cat([q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda()) for b in srcs]).contiguous()
+    peak, _ = measured_peak()
+
+    def tev(fn, reps=30):
+        for _ in range(3):
+            fn()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        z.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / reps
+
+    inp = q.empty_fields(lat, "f32r12", nrhs).normal_()
+    out = q.empty_fields(lat, "f32r12", nrhs)
+    one_in, one_out = inp[: inp.numel() // nrhs].contiguous(), q.empty_field(lat, "f32r12")
+    t_m = tev(lambda: q.qex_dslash_mrhs(lat, "f32r12", fatr, None, 0.0, 1, nrhs, inp, out))
+    t_1 = tev(lambda: q.qex_dslash(lat, "f32r12", fatr, None, 0.0, 1, one_in, one_out))
+    mbytes = (384 + nrhs * 48) * vh
+    print(json.dumps({"mrhs": "dslash", "lattice": list(dims), "nrhs": nrhs, "prec": "f32r12",
+                      "batched_ms": round(t_m, 4), "single_ms": round(t_1, 4),
+                      "per_rhs_speedup": round(t_1 * nrhs / t_m, 2),
+                      "batched_GB/s": round(mbytes / (t_m * 1e-3) / 1e9, 1),
+                      "batched_frac": round(mbytes / (t_m * 1e-3) / 1e9 / peak, 4),
+                      "bytes_per_site": 384 + nrhs * 48}), flush=True)
+    X = torch.zeros_like(B)
+    q.qex_cg_mrhs(lat, "f32r12", fat64, None, fatr, None, 0.0, MRHS_MASS, nrhs, B, X, tol=TOL, delta=DELTA)
+    X.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, stm = q.qex_cg_mrhs(lat, "f32r12", fat64, None, fatr, None, 0.0, MRHS_MASS, nrhs, B, X, tol=TOL, delta=DELTA)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    its = []
+    for r in range(nrhs):
+        x1 = torch.zeros(n64, dtype=torch.float64, device="cuda")
+        _, s1 = q.qex_cg(lat, "f32r12", fat64, None, fatr, None, 0.0, MRHS_MASS, B[r * n64:(r + 1) * n64].contiguous(),
+                         x1, tol=TOL, delta=DELTA)
+        its.append(s1["iters"])
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    print(json.dumps({"mrhs": "cg", "lattice": list(dims), "nrhs": nrhs, "mass": MRHS_MASS, "links": "Haar",
+                      "batched_s": round(t_batched, 4), "sequential_single_s": round(t_single, 4),
+                      "speedup": round(t_single / t_batched, 2),
+                      "batched_iters": [x["iters"] for x in stm], "single_iters": its,
+                      "max_true_rel_resid": max(x["true_rel_resid"] for x in stm),
+                      "all_converged": all(x["converged"] for x in stm)}), flush=True)
+
+
 def main():
     args = parse()
-    if args.sweep:
+    if args.mrhs:
+        run_mrhs(args)
+    elif args.sweep:
         run_sweep(args)
     elif args.dslash_only:
         run_dslash_only()

@@ -162,6 +162,18 @@ qex_status qex_convert_field(const qex_lattice *lat, qex_prec from, const void *
 qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                       double c_naik, int out_parity, const void *in, void *out, void *stream);
 
+/* Largest number of right-hand sides of the multi-RHS calls. */
+#define QEX_MRHS_MAX 64
+
+/* Multi-RHS Dslash: out_r = D_{p,1-p} in_r for r = 0..nrhs-1, with each link
+ * read from memory once for all right-hand sides (the paper benchmarks one
+ * right-hand side, Fig. 1; batching them cuts the link traffic per vector by
+ * nrhs).  `in` and `out` hold nrhs half fields back to back (field r starts
+ * at r * qex_field_bytes(lat, prec)); they must not overlap.  1 <= nrhs <=
+ * QEX_MRHS_MAX.  Other arguments and errors as qex_dslash. */
+qex_status qex_dslash_mrhs(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
+                           double c_naik, int out_parity, int nrhs, const void *in, void *out, void *stream);
+
 /* out = (m^2 - D_eo D_oe) in on even sites; tmp_odd is a caller half field
  * (odd sites) that receives D_oe in. */
 qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
@@ -252,6 +264,19 @@ qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, con
  * an extent < 4). */
 qex_status qex_force(const qex_lattice *lat, const void *fat64, const void *lng64, double c_naik,
                      const void *x_even, const void *y_odd, int kind, void *out_fat, void *out_lng, void *stream);
+
+/* Multi-RHS CG: solves (m^2 - D_eo D_oe) x_r = b_r for r = 0..nrhs-1 with
+ * every operator application shared (qex_dslash_mrhs), as qex_cg does for
+ * one right-hand side.  b64, x64: nrhs F64 even half fields back to back;
+ * x64 holds the initial guesses and receives the solutions.  The solves
+ * iterate in lockstep; each stops (is frozen) when its own FP64 true residual
+ * meets tol; a reliable update requested by any running one is done for all
+ * running ones.  stats (may be NULL) receives nrhs entries.  Synchronises the
+ * stream.  Errors as qex_cg (QEX_ERR_NOT_CONVERGED if any right-hand side did
+ * not converge). */
+qex_status qex_cg_mrhs(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
+                       const void *fat32, const void *lng32, double c_naik, double mass, int nrhs, const void *b64,
+                       void *x64, double tol, int maxiter, double delta, void *stream, qex_cg_stats *stats);
 
 /* End-to-end solve from HOST memory (the call for users whose fields live
  * on the host).  host_fat (and host_lng, or NULL) are canonical complex-double

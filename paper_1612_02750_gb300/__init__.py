@@ -86,6 +86,8 @@ def load():
         "qex_cg": (i, [vp, i, vp, vp, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_cg_host": (i, [vp, i, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_force": (i, [vp, vp, vp, d, vp, vp, i, vp, vp, vp]),
+        "qex_dslash_mrhs": (i, [vp, i, vp, vp, d, i, i, vp, vp, vp]),
+        "qex_cg_mrhs": (i, [vp, i, vp, vp, vp, vp, d, d, i, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -104,7 +106,8 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_force", "qex_launch_count", "qex_last_error", "qex_version"]
+            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_launch_count", "qex_last_error",
+            "qex_version"]
 
 
 def _check(status: int):
@@ -286,6 +289,21 @@ def qex_dslash(lat: Lattice, prec, fat, lng, c_naik: float, out_parity: int, inp
     return out
 
 
+def empty_fields(lat: Lattice, prec, nrhs: int, device="cuda"):
+    """nrhs half fields back to back (the multi-RHS layout)."""
+    p = _prec(prec)
+    n = qex_field_bytes(lat, p) // _DTYPE[p].itemsize
+    return torch.empty(nrhs * n, dtype=_DTYPE[p], device=device)
+
+
+def qex_dslash_mrhs(lat: Lattice, prec, fat, lng, c_naik: float, out_parity: int, nrhs: int, inp, out=None,
+                    stream=None):
+    out = empty_fields(lat, prec, nrhs) if out is None else out
+    _check(load().qex_dslash_mrhs(lat.handle, _prec(prec), _ptr(fat), _ptr(lng), float(c_naik), int(out_parity),
+                                  int(nrhs), _ptr(inp), _ptr(out), _stream(stream)))
+    return out
+
+
 def qex_normal_op(lat: Lattice, prec, fat, lng, c_naik: float, mass: float, inp, out=None, tmp_odd=None,
                   stream=None):
     out = empty_field(lat, prec) if out is None else out
@@ -419,6 +437,19 @@ def qex_cg_host(lat: Lattice, inner, host_fat, host_lng, c_naik: float, mass: fl
 
 def qex_launch_count() -> int:
     return int(load().qex_launch_count())
+
+
+def qex_cg_mrhs(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, mass: float, nrhs: int, b64, x64,
+                tol: float = 1e-10, maxiter: int = 100000, delta: float = 0.1, stream=None, check: bool = True):
+    """Multi-RHS solve; b64/x64 hold nrhs F64 even half fields back to back.
+    Returns (status, list of per-RHS stats dicts)."""
+    stats = (CgStats * int(nrhs))()
+    st = load().qex_cg_mrhs(lat.handle, _prec(inner), _ptr(fat64), _ptr(lng64), _ptr(fat32), _ptr(lng32),
+                            float(c_naik), float(mass), int(nrhs), _ptr(b64), _ptr(x64), float(tol), int(maxiter),
+                            float(delta), _stream(stream), stats)
+    if check:
+        _check(st)
+    return st, [stats[k].as_dict() for k in range(int(nrhs))]
 
 
 def qex_last_error() -> str:

@@ -87,6 +87,8 @@ qex_status ensure_scratch(qex_lattice *lat) {
     int nb = blocks_for(lat->vh, kDslashBlock < kBlock ? kDslashBlock : kBlock);
     int nbb = blas_blocks(lat);
     lat->partials_len = 2 * (nb > nbb ? nb : nbb);
+    const int mrhs = (sm_count() * 8 + 1) * kMaxRhs;  // per-block, per-right-hand-side partials
+    if (lat->partials_len < mrhs) lat->partials_len = mrhs;
     QEX_CUDA(cudaMalloc(&lat->partials, sizeof(double) * lat->partials_len));
     QEX_CUDA(cudaMalloc(&lat->counter, sizeof(unsigned int) * 4));
     QEX_CUDA(cudaMemset(lat->counter, 0, sizeof(unsigned int) * 4));

@@ -68,6 +68,44 @@ struct DslashArgs {
 
 qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
 
+// ------------------------------------------------------------ multi-RHS CG
+// Per-right-hand-side CG scalars (all active right-hand sides iterate in
+// lockstep; a converged one is frozen by its `active` flag).
+constexpr int kMaxRhs = QEX_MRHS_MAX;
+struct MrhsScalars {
+    double rr[kMaxRhs], pAp[kMaxRhs], alpha[kMaxRhs], beta[kMaxRhs], bb[kMaxRhs], stop2[kMaxRhs],
+        rmax2[kMaxRhs], true_rr[kMaxRhs];
+    int active[kMaxRhs];   // still iterating
+    int done[kMaxRhs];     // true residual met tol
+    int iters[kMaxRhs];    // iterations while active
+    double tol2, delta2;
+    int nrhs;
+    int iter;              // lockstep iteration count: its parity selects the p buffers
+    int maxiter;
+    int need_ru, halt, error;
+    int reliable_updates;
+    int nactive;
+};
+
+struct MrhsArgs {
+    qex_prec prec;
+    const void *fat, *lng;
+    double c3;
+    int out_parity;
+    int nrhs;
+    const void *in;       // EPI_PLAIN / EPI_NORMAL / EPI_RESID input fields
+    void *out;
+    int epi;
+    const void *q;        // EPI_RESID: x fields
+    const double *b;      // EPI_RESID: b fields (FP64)
+    double m2;
+    MrhsScalars *S;       // NULL: plain application, no masking
+    const void *r;        // EPI_PUPD
+    void *pbuf[2];        // EPI_PUPD / EPI_NORMAL (q = p_new)
+};
+
+qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t st);
+
 // x += alpha p_new; r -= alpha ap; ||r||^2 -> S (rr, beta, flags); sets the
 // graph conditions when ctl.active.
 qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, void *const pbuf[2],

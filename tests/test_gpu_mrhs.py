@@ -1,0 +1,151 @@
+"""Multi-right-hand-side Dslash and CG against the single-RHS path and the
+oracle."""
+
+import numpy as np
+import pytest
+
+import fieldgen as fg
+
+pytestmark = pytest.mark.gpu
+
+C3 = -1.0 / 24.0
+TOL = {"f64": 1e-14, "f32": 1e-6, "f32r12": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_02750_gb300 import build
+
+    build.build()
+    import paper_1612_02750_gb300 as mod
+
+    mod.load()
+    return mod
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 5, 16, 37])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12"])
+@pytest.mark.parametrize("naik", [False, True])
+def test_dslash_mrhs_matches_single(q, nrhs, prec, naik):
+    """Each output field of the batched operator equals the single-RHS
+    operator on that field (same arithmetic order; ragged RHS groups and a
+    ragged site tail)."""
+    import torch
+
+    dims = (6, 4, 4, 10)
+    s = fg.rng_streams(61)
+    u = fg.random_links(dims, "haar", s["links"])
+    lat = q.Lattice(dims)
+    fat64 = q.qex_pack_links(lat, "f64", dev(u))
+    fat = fat64 if prec == "f64" else q.qex_convert_links(lat, "f64", fat64, prec)
+    lng = None
+    if naik:
+        w = fg.random_links(dims, "gauss3", s["long_links"])
+        lng = q.qex_pack_links(lat, "f64" if prec == "f64" else "f32", dev(w))
+    n = q.qex_field_bytes(lat, prec) // (8 if prec == "f64" else 4)
+    for out_p in (0, 1):
+        inp = q.empty_fields(lat, prec, nrhs).normal_()
+        out = q.qex_dslash_mrhs(lat, prec, fat, lng, C3, out_p, nrhs, inp)
+        for r in range(nrhs):
+            ref = q.qex_dslash(lat, prec, fat, lng, C3, out_p, inp[r * n:(r + 1) * n].contiguous())
+            got = out[r * n:(r + 1) * n]
+            assert torch.linalg.norm(got - ref).item() <= TOL[prec] * torch.linalg.norm(ref).item(), (out_p, r)
+
+
+def test_dslash_mrhs_matches_oracle(q, oracle_mod):
+    dims = (8, 4, 6, 8)
+    s = fg.rng_streams(62)
+    u = fg.random_links(dims, "exp", s["links"], 0.4)
+    w = fg.random_links(dims, "gauss3", s["long_links"])
+    lat = q.Lattice(dims)
+    fat = q.qex_pack_links(lat, "f64", dev(u))
+    lng = q.qex_pack_links(lat, "f64", dev(w))
+    fields = [fg.gaussian_field(s["source"], dims) for _ in range(6)]
+    inp = torch_cat(q, [q.qex_pack_field(lat, "f64", 1, dev(f)) for f in fields])
+    out = q.qex_dslash_mrhs(lat, "f64", fat, lng, C3, 0, 6, inp)
+    n = q.qex_field_bytes(lat, "f64") // 8
+    ev = fg.even_mask(dims)
+    for r, f in enumerate(fields):
+        got = q.qex_unpack_field(lat, "f64", 0, out[r * n:(r + 1) * n].contiguous()).cpu().numpy()
+        ref = oracle_mod.dslash_parity(dims, u, f, 0, w, C3)
+        assert relerr(got[ev], ref[ev]) <= 1e-13
+
+
+def torch_cat(q, parts):
+    import torch
+
+    return torch.cat(parts).contiguous()
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32r12"])
+@pytest.mark.parametrize("naik", [False, True])
+def test_cg_mrhs(q, oracle_mod, inner, naik):
+    """Five sources (one of them zero) solved together: every solution has an
+    oracle-recomputed true residual <= 1.05e-10 and agrees with the single-RHS
+    solve of the same source."""
+    import torch
+
+    dims = (8, 8, 4, 8)
+    m = 0.1
+    s = fg.rng_streams(63)
+    u = fg.random_links(dims, "haar", s["links"])
+    w = fg.random_links(dims, "gauss3", s["long_links"]) if naik else None
+    c3 = C3 if naik else 0.0
+    ev = fg.even_mask(dims)
+    srcs = []
+    for r in range(5):
+        b = fg.gaussian_field(s["source"], dims) * (0.0 if r == 2 else 10.0 ** (r - 2))
+        b[~ev] = 0
+        srcs.append(b)
+    lat = q.Lattice(dims)
+    fat64 = q.qex_pack_links(lat, "f64", dev(u))
+    lng64 = q.qex_pack_links(lat, "f64", dev(w)) if naik else None
+    fat32 = q.qex_convert_links(lat, "f64", fat64, inner) if inner != "f64" else None
+    lng32 = q.qex_convert_links(lat, "f64", lng64, "f32") if (naik and inner != "f64") else None
+    B = torch_cat(q, [q.qex_pack_field(lat, "f64", 0, dev(b)) for b in srcs])
+    X = torch.zeros_like(B)
+    st, stats = q.qex_cg_mrhs(lat, inner, fat64, lng64, fat32, lng32, c3, m, 5, B, X, tol=1e-10, delta=0.1)
+    assert st == 0 and all(x["converged"] for x in stats), stats
+    n = q.qex_field_bytes(lat, "f64") // 8
+    for r, b in enumerate(srcs):
+        x = q.qex_unpack_field(lat, "f64", 0, X[r * n:(r + 1) * n].contiguous()).cpu().numpy()
+        if r == 2:
+            assert not x.any()
+            continue
+        tr = oracle_mod.true_residual(dims, u, b, x, m, w, c3)
+        assert tr <= 1.05e-10, (r, tr)
+        x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        q.qex_cg(lat, inner, fat64, lng64, fat32, lng32, c3, m, B[r * n:(r + 1) * n].contiguous(), x1, tol=1e-10,
+                 delta=0.1)
+        xs = q.qex_unpack_field(lat, "f64", 0, x1).cpu().numpy()
+        assert relerr(x[ev], xs[ev]) <= 1e-7
+
+
+def test_cg_mrhs_errors(q):
+    import torch
+
+    lat = q.Lattice((4, 4, 4, 4))
+    fat = q.empty_links(lat, "f64")
+    B = q.empty_fields(lat, "f64", 2).zero_()
+    X = torch.zeros_like(B)
+    with pytest.raises(q.QexError) as e:
+        q.qex_cg_mrhs(lat, "f64", fat, None, None, None, 0.0, 0.1, 0, B, X)
+    assert e.value.status == 1
+    with pytest.raises(q.QexError) as e:
+        q.qex_cg_mrhs(lat, "f64", fat, None, None, None, 0.0, 0.1, 65, B, X)
+    assert e.value.status == 1
+    st, stats = q.qex_cg_mrhs(lat, "f64", fat, None, None, None, 0.0, 0.1, 2, B, X)  # zero sources
+    assert st == 0 and all(s["converged"] for s in stats) and not X.any()
