@@ -3,21 +3,23 @@
 // epilogues of the multi-RHS CG.
 //
 // Fields: N half fields back to back (field r starts at r * qex_field_bytes).
-// A block covers 32 consecutive output sites (threadIdx.x) and up to eight
-// groups of four right-hand sides (threadIdx.y, one warp each; more groups
-// go to blockIdx.y); the warps of a block request the same link addresses at
-// about the same time, so a link line comes from HBM once and is served to
-// the other warps from L1/L2.  Per site the algorithmic traffic is the 8 (16
-// with Naik) links once plus, per right-hand side, the input vector once and
-// the output once.  The reducing epilogues run a persistent grid-stride loop
-// and reduce per right-hand side in a fixed order (bit-reproducible).
+// Per site the algorithmic traffic is the 8 (16 with Naik) links once plus,
+// per right-hand side, the input vector once and the output once.  The
+// reducing epilogues run a persistent grid-stride loop and reduce per
+// right-hand side in a fixed order (bit-reproducible).
 #include "qex_kernels.cuh"
 
 namespace qex {
 
-constexpr int kMrhsSites = 32;  // output sites per block (one warp row)
-constexpr int kMrhsGroup = 4;   // right-hand sides per thread
-constexpr int kMrhsWarps = 8;   // right-hand-side groups per block (more go to blockIdx.y)
+// Thread mapping: lane = 4 * site_in_warp + k, one right-hand side per
+// thread; the four lanes of a site load the same link words (one broadcast
+// transaction) and their own vectors.  A block is 8 warps = 64 sites x 4
+// right-hand sides; linear block b covers site block b / ngroups and
+// right-hand-side group b % ngroups, so the blocks that reuse a link run
+// back to back and find it in L2.
+constexpr int kMrhsGroup = 4;                  // right-hand sides per site within a warp
+constexpr int kMrhsBlock = 256;                // threads per block
+constexpr int kMrhsSitesPerBlock = kMrhsBlock / kMrhsGroup;
 
 template <typename R, int FMT>
 __device__ __forceinline__ Mat3<R> load_fat_m(const R *base, size_t vh, int p, int mu, int i) {
@@ -32,7 +34,7 @@ struct MParams {
     Geom g;
     const R *fat, *lng;
     R c3;
-    int p, nrhs;
+    int p, nrhs, ngroups;
     const R *in;
     R *out;
     const R *q;
@@ -64,23 +66,19 @@ __device__ __forceinline__ Vec3<R> mrhs_in(const MParams<R> &P, const R *pold, R
 }
 
 template <typename R, int FMT, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kMrhsSites * kMrhsWarps) dslash_mrhs_kernel(const MParams<R> P) {
+__global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParams<R> P) {
+    __shared__ double wsum[kMrhsBlock / 32][kMrhsGroup];
     __shared__ unsigned int is_last;
     MrhsScalars *S = P.S;
     if (P.check_halt && S->halt) return;  // uniform over the grid
-    const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * kMrhsGroup;
     const Geom &g = P.g;
     const size_t vh = (size_t)g.vh;
     const size_t fstride = 6 * vh;  // reals per half field
     const int p = P.p;
-    bool act[kMrhsGroup];
-    R beta[kMrhsGroup];
-#pragma unroll
-    for (int k = 0; k < kMrhsGroup; ++k) {
-        const int r = r0 + k;
-        act[k] = r < P.nrhs && (S == nullptr || S->active[r]);
-        beta[k] = (EPI == EPI_PUPD && act[k]) ? (R)S->beta[r] : R(0);
-    }
+    const int k = threadIdx.x & (kMrhsGroup - 1);
+    const int sub = threadIdx.x / kMrhsGroup;
+    const int nsb = (int)((vh + kMrhsSitesPerBlock - 1) / kMrhsSitesPerBlock);
+    const int total = nsb * P.ngroups;
     const R *pold = nullptr;
     R *pnew = nullptr;
     if (EPI == EPI_PUPD || EPI == EPI_NORMAL) {
@@ -88,128 +86,135 @@ __global__ void __launch_bounds__(kMrhsSites * kMrhsWarps) dslash_mrhs_kernel(co
         pold = (it & 1) ? P.pbuf1 : P.pbuf0;
         pnew = (it & 1) ? P.pbuf0 : P.pbuf1;
     }
-    double part[kMrhsGroup] = {0.0, 0.0, 0.0, 0.0};
-
-    for (int i = blockIdx.x * kMrhsSites + threadIdx.x; i < g.vh; i += gridDim.x * kMrhsSites) {
+    double part = 0.0;
+    // reducing launches have gridDim.x a multiple of ngroups: the group is fixed per block
+    for (int bl = blockIdx.x; bl < total; bl += gridDim.x) {
+        const int grp = bl % P.ngroups;
+        const int rh = grp * kMrhsGroup + k;
+        const int i = (bl / P.ngroups) * kMrhsSitesPerBlock + sub;
+        const bool act = i < g.vh && rh < P.nrhs && (S == nullptr || S->active[rh]);
+        if (!act) continue;
+        const R beta = (EPI == EPI_PUPD) ? (R)S->beta[rh] : R(0);
+        const size_t off = (size_t)rh * fstride;
         const Site s = site_of(g, p, i);
-        Vec3<R> acc[kMrhsGroup];
+        Vec3<R> acc;
 #pragma unroll
-        for (int k = 0; k < kMrhsGroup; ++k)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) acc[k].c[a].re = acc[k].c[a].im = R(0);
+        for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = R(0);
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             const R eta = eta_bit(s, mu) ? R(-1) : R(1);
-#pragma unroll
-            for (int hop = 0; hop < (NAIK ? 4 : 2); ++hop) {
-                const int k3 = hop >= 2 ? 3 : 1;
-                const bool fwd = (hop & 1) == 0;
-                const int j = hop_index(g, s, mu, fwd ? k3 : -k3);
-                Mat3<R> u;
-                if (hop >= 2)
-                    u = load_link(P.lng, vh, fwd ? p : 1 - p, mu, fwd ? i : j);
-                else
-                    u = load_fat_m<R, FMT>(P.fat, vh, fwd ? p : 1 - p, mu, fwd ? i : j);
-                const int bc = fwd ? bc_bit_fwd(g, s, mu, k3) : bc_bit_bwd(g, s, mu, k3);
-                R sg = (bc ? -eta : eta) * (hop >= 2 ? P.c3 : R(1));
-                if (!fwd) sg = -sg;
-#pragma unroll
-                for (int k = 0; k < kMrhsGroup; ++k) {
-                    if (act[k]) {
-                        const Vec3<R> v = mrhs_in<R, EPI>(P, pold, beta[k], (size_t)(r0 + k) * fstride, vh, j);
-                        if (fwd)
-                            acc_mv(acc[k], sg, u, v);
-                        else
-                            acc_mdv(acc[k], sg, u, v);
-                    }
+            {
+                const int j = hop_index(g, s, mu, 1);
+                const Mat3<R> u = load_fat_m<R, FMT>(P.fat, vh, p, mu, i);
+                acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
+            }
+            {
+                const int j = hop_index(g, s, mu, -1);
+                const Mat3<R> u = load_fat_m<R, FMT>(P.fat, vh, 1 - p, mu, j);
+                acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
+            }
+            if (NAIK) {
+                const R e3 = P.c3 * eta;
+                {
+                    const int j = hop_index(g, s, mu, 3);
+                    const Mat3<R> u = load_link(P.lng, vh, p, mu, i);
+                    acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
+                }
+                {
+                    const int j = hop_index(g, s, mu, -3);
+                    const Mat3<R> u = load_link(P.lng, vh, 1 - p, mu, j);
+                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
                 }
             }
         }
+        if constexpr (EPI == EPI_PLAIN) {
+            store_vec(P.out + off, vh, i, acc);
+        } else if constexpr (EPI == EPI_PUPD) {
+            store_vec(P.out + off, vh, i, acc);
+            store_vec(pnew + off, vh, i, mrhs_in<R, EPI>(P, pold, beta, off, vh, i));
+        } else if constexpr (EPI == EPI_NORMAL) {
+            const Vec3<R> qv = load_vec(pnew + off, vh, i);
+            Vec3<R> o;
+            R d = R(0);
 #pragma unroll
-        for (int k = 0; k < kMrhsGroup; ++k) {
-            if (!act[k]) continue;
-            const size_t off = (size_t)(r0 + k) * fstride;
-            if constexpr (EPI == EPI_PLAIN) {
-                store_vec(P.out + off, vh, i, acc[k]);
-            } else if constexpr (EPI == EPI_PUPD) {
-                store_vec(P.out + off, vh, i, acc[k]);
-                store_vec(pnew + off, vh, i, mrhs_in<R, EPI>(P, pold, beta[k], off, vh, i));
-            } else if constexpr (EPI == EPI_NORMAL) {
-                const Vec3<R> qv = load_vec(pnew + off, vh, i);
-                Vec3<R> o;
-                R d = R(0);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    o.c[a].re = fma(P.m2, qv.c[a].re, -acc[k].c[a].re);
-                    o.c[a].im = fma(P.m2, qv.c[a].im, -acc[k].c[a].im);
-                    d = fma(qv.c[a].re, o.c[a].re, d);
-                    d = fma(qv.c[a].im, o.c[a].im, d);
-                }
-                store_vec(P.out + off, vh, i, o);
-                part[k] += (double)d;
-            } else {  // EPI_RESID, FP64: out = b - m^2 x + D in
-                const Vec3<R> qv = load_vec(P.q + off, vh, i);
-                const Vec3<double> bv = load_vec(P.b + off, vh, i);
-                Vec3<R> o;
-                double d = 0.0;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    o.c[a].re = (R)bv.c[a].re - fma(P.m2, qv.c[a].re, -acc[k].c[a].re);
-                    o.c[a].im = (R)bv.c[a].im - fma(P.m2, qv.c[a].im, -acc[k].c[a].im);
-                    d = fma((double)o.c[a].re, (double)o.c[a].re, d);
-                    d = fma((double)o.c[a].im, (double)o.c[a].im, d);
-                }
-                store_vec(P.out + off, vh, i, o);
-                part[k] += d;
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = fma(P.m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = fma(P.m2, qv.c[a].im, -acc.c[a].im);
+                d = fma(qv.c[a].re, o.c[a].re, d);
+                d = fma(qv.c[a].im, o.c[a].im, d);
             }
+            store_vec(P.out + off, vh, i, o);
+            part += (double)d;
+        } else {  // EPI_RESID, FP64: out = b - m^2 x + D in
+            const Vec3<R> qv = load_vec(P.q + off, vh, i);
+            const Vec3<double> bv = load_vec(P.b + off, vh, i);
+            Vec3<R> o;
+            double d = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = (R)bv.c[a].re - fma(P.m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = (R)bv.c[a].im - fma(P.m2, qv.c[a].im, -acc.c[a].im);
+                d = fma((double)o.c[a].re, (double)o.c[a].re, d);
+                d = fma((double)o.c[a].im, (double)o.c[a].im, d);
+            }
+            store_vec(P.out + off, vh, i, o);
+            part += d;
         }
     }
     if constexpr (EPI == EPI_PLAIN || EPI == EPI_PUPD) {
         return;
     } else {
-        // per right-hand side: warp sum -> partials[blockIdx.x][r]; the last
-        // block sums each r over blockIdx.x in a fixed order
+        // per right-hand side of this block's group: lanes with equal k sum
+        // within the warp, then warps in order -> partials[blockIdx.x][k]
+        double v = part;
 #pragma unroll
-        for (int k = 0; k < kMrhsGroup; ++k) {
-            double v = part[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (threadIdx.x == 0 && r0 + k < P.nrhs) P.partials[(size_t)blockIdx.x * P.nrhs + r0 + k] = v;
+        for (int o = 16; o >= kMrhsGroup; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane < kMrhsGroup) wsum[warp][lane] = v;
+        __syncthreads();
+        if (threadIdx.x < kMrhsGroup) {
+            double t = 0.0;
+            for (int w = 0; w < kMrhsBlock / 32; ++w) t += wsum[w][threadIdx.x];
+            P.partials[(size_t)blockIdx.x * kMrhsGroup + threadIdx.x] = t;
         }
         __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
+        if (threadIdx.x == 0) {
             __threadfence();
             const unsigned int t = atomicAdd(P.counter, 1u);
-            is_last = (t == gridDim.x * gridDim.y - 1) ? 1u : 0u;
+            is_last = (t == gridDim.x - 1) ? 1u : 0u;
         }
         __syncthreads();
         if (!is_last) return;
         __threadfence();
-        for (int r = threadIdx.y; r < P.nrhs; r += blockDim.y) {
-            double v = 0.0;
-            for (int bx = threadIdx.x; bx < (int)gridDim.x; bx += 32) v += __ldcg(P.partials + (size_t)bx * P.nrhs + r);
+        // right-hand side r = grp * 4 + k lives in blocks bx = grp (mod ngroups)
+        const int nw = kMrhsBlock / 32;
+        for (int r = warp; r < P.nrhs; r += nw) {
+            const int grp = r / kMrhsGroup, kk = r % kMrhsGroup;
+            double t = 0.0;
+            for (int bx = grp + lane * P.ngroups; bx < (int)gridDim.x; bx += 32 * P.ngroups)
+                t += __ldcg(P.partials + (size_t)bx * kMrhsGroup + kk);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (threadIdx.x != 0 || !S->active[r]) continue;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane != 0 || !S->active[r]) continue;
             if constexpr (EPI == EPI_NORMAL) {
-                S->pAp[r] = v;
-                if (!(v > 0.0) || !isfinite(v)) {
-                    S->error = isfinite(v) ? 2 : 1;
+                S->pAp[r] = t;
+                if (!(t > 0.0) || !isfinite(t)) {
+                    S->error = isfinite(t) ? 2 : 1;
                     S->halt = 1;
                 } else {
-                    S->alpha[r] = S->rr[r] / v;
+                    S->alpha[r] = S->rr[r] / t;
                 }
             } else {
-                S->true_rr[r] = v;
-                if (!isfinite(v)) {
+                S->true_rr[r] = t;
+                if (!isfinite(t)) {
                     S->error = 1;
                     S->halt = 1;
                     continue;
                 }
-                S->beta[r] = S->rr[r] > 0.0 ? v / S->rr[r] : 0.0;
-                S->rr[r] = v;
-                S->rmax2[r] = v;
-                if (v <= S->stop2[r]) {
+                S->beta[r] = S->rr[r] > 0.0 ? t / S->rr[r] : 0.0;
+                S->rr[r] = t;
+                S->rmax2[r] = t;
+                if (t <= S->stop2[r]) {
                     S->done[r] = 1;
                     S->active[r] = 0;
                 }
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(kMrhsSites * kMrhsWarps) dslash_mrhs_kernel(co
         }
         if constexpr (EPI == EPI_RESID) {
             __syncthreads();
-            if (threadIdx.x == 0 && threadIdx.y == 0) {
+            if (threadIdx.x == 0) {
                 int n = 0;
                 for (int r = 0; r < P.nrhs; ++r) n += S->active[r];
                 S->nactive = n;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(kMrhsSites * kMrhsWarps) dslash_mrhs_kernel(co
                 S->halt = (n == 0 || S->iter >= S->maxiter || S->error) ? 1 : 0;
             }
         }
-        if (threadIdx.x == 0 && threadIdx.y == 0) *P.counter = 0u;
+        if (threadIdx.x == 0) *P.counter = 0u;
     }
 }
 
@@ -239,6 +244,7 @@ static void launch_m(const qex_lattice *lat, const MrhsArgs &a, cudaStream_t st)
     P.c3 = (R)a.c3;
     P.p = a.out_parity;
     P.nrhs = a.nrhs;
+    P.ngroups = (a.nrhs + kMrhsGroup - 1) / kMrhsGroup;
     P.in = (const R *)a.in;
     P.out = (R *)a.out;
     P.q = (const R *)a.q;
@@ -251,17 +257,16 @@ static void launch_m(const qex_lattice *lat, const MrhsArgs &a, cudaStream_t st)
     P.pbuf1 = (R *)a.pbuf[1];
     P.partials = lat->partials;
     P.counter = lat->counter;
-    const int groups = (a.nrhs + kMrhsGroup - 1) / kMrhsGroup;
-    const int wy = groups < kMrhsWarps ? groups : kMrhsWarps;
-    const int full = (int)((lat->vh + kMrhsSites - 1) / kMrhsSites);
-    int gx = full;
-    if (EPI == EPI_NORMAL || EPI == EPI_RESID) {  // persistent grid for the reducing variants
-        const int cap = sm_count() * 4;
-        gx = full < cap ? full : cap;
+    const int nsb = (int)((lat->vh + kMrhsSitesPerBlock - 1) / kMrhsSitesPerBlock);
+    const int total = nsb * P.ngroups;
+    int gx = total;
+    if (EPI == EPI_NORMAL || EPI == EPI_RESID) {  // persistent grid, a multiple of ngroups
+        int cap = sm_count() * 3;
+        cap -= cap % P.ngroups;
+        if (cap < P.ngroups) cap = P.ngroups;
+        gx = total < cap ? total : cap;
     }
-    dim3 block(kMrhsSites, wy);
-    dim3 grid(gx, (groups + wy - 1) / wy);
-    dslash_mrhs_kernel<R, FMT, NAIK, EPI><<<grid, block, 0, st>>>(P);
+    dslash_mrhs_kernel<R, FMT, NAIK, EPI><<<gx, kMrhsBlock, 0, st>>>(P);
 }
 
 template <typename R, int FMT, bool NAIK>
@@ -280,7 +285,7 @@ qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t 
     if (a.epi == EPI_NORMAL || a.epi == EPI_RESID) {
         qex_status s = ensure_scratch(lat);
         if (s) return s;
-        const size_t need = (size_t)(sm_count() * 4 + 1) * a.nrhs;
+        const size_t need = (size_t)(sm_count() * 3 + 1) * kMrhsGroup;
         if ((size_t)lat->partials_len < need) {
             set_error("internal: partials buffer too small for %d right-hand sides", a.nrhs);
             return QEX_ERR_ARG;
