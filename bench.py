@@ -5,8 +5,8 @@ A step is one pass of the whole path on the 32^4 workload (links
 exp(i 0.3 H), m = 0.01, one Gaussian even-site source): pack the canonical
 FP64 links into the internal layout, round the FP32 copy, pack the source,
 solve (m^2 - D_eo D_oe) x = b by mixed-precision CG (FP32 inner iteration on
-two-row FP32 links, FP64 reliable updates) to a true relative residual of
-1e-10, and unpack the
+two-row 16-bit fixed-point links, FP64 reliable updates) to a true relative
+residual of 1e-10, and unpack the
 solution.  ``value`` is solves per second over all ranks with inputs resident
 in HBM; ``e2e`` is the same through ``qex_cg_host`` from page-locked host
 buffers (copies inside the timed region).  Ranks are independent replicas
@@ -34,10 +34,10 @@ METRIC = "Dslash GB/s & GFLOP/s vs HBM roofline; CG time to 1e-10 residual, mixe
 WORKLOAD = "cfg32"
 TOL = 1e-10
 DELTA = 0.01           # reliable-update threshold (sweep on this workload: same iterations, fewest updates)
-INNER = "f32r12"       # inner CG precision: FP32 fields, two-row FP32 SU(3) links
+INNER = "f32r12h"      # inner CG precision: FP32 fields, two-row 16-bit fixed-point SU(3) links
 FLOP_NN = 570          # flops per output site of the one-hop Dslash (8 mat-vecs x 66 + 7 x 6 adds)
 # 8 links + 8 input vectors counted once + 1 output vector, per output site
-BYTES_NN = {"f64": 1248, "f32": 624, "f32r12": 432}
+BYTES_NN = {"f64": 1248, "f32": 624, "f32r12": 432, "f32r12h": 240}
 L2_BYTES = 135528448   # sm_103a L2 (cudaDevAttrL2CacheSize on GB300)
 FALLBACK_HBM_GBS = 6800.0
 
@@ -60,8 +60,8 @@ def parse():
                     help="multi-RHS case: 24^4 Haar links, 16 Gaussian sources, batched Dslash and CG against "
                          "single-RHS calls")
     ap.add_argument("--dslash-only", action="store_true",
-                    help="profiling case: two launches each of the two-row FP32, FP32 and FP64 one-hop Dslash "
-                         "on the workload, no timing")
+                    help="profiling case: two launches each of the 16-bit two-row, two-row FP32, FP32 and FP64 "
+                         "one-hop Dslash on the workload, no timing")
     return ap.parse_args()
 
 
@@ -313,17 +313,19 @@ def run_native(args):
         return a.elapsed_time(z) / reps
 
     full32 = q.qex_convert_links(lat, "f64", fat64, "f32")
-    times = {"f32r12": time_dslash("f32r12", fat32), "f32": time_dslash("f32", full32), "f64": time_dslash("f64", fat64)}
-    del full32
+    r12 = q.qex_convert_links(lat, "f64", fat64, "f32r12")
+    times = {"f32r12h": time_dslash("f32r12h", fat32), "f32r12": time_dslash("f32r12", r12),
+             "f32": time_dslash("f32", full32), "f64": time_dslash("f64", fat64)}
+    del full32, r12
     peak, peak_kind = measured_peak()
 
     def gbs(prec):
         return BYTES_NN[prec] * vh / (times[prec] * 1e-3) / 1e9
 
     ach = gbs(INNER)
-    roofline = {"bound": "hbm", "kernel": "dslash_kernel<float, two-row links, one-hop> (D_oe, 32^4)",
+    roofline = {"bound": "hbm", "kernel": "dslash_kernel<float, 16-bit two-row links, one-hop> (D_oe, 32^4)",
                 "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                "traffic": ncu_traffic("dslash_f32r12_nn_32^4"), "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "traffic": ncu_traffic("dslash_f32r12h_nn_32^4"), "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "bytes_per_site": BYTES_NN[INNER], "sites_per_launch": vh, "avg_launch_ms": round(times[INNER], 5)}
     dslash = {p: {"ms": round(t, 5), "GB/s": round(gbs(p), 1), "frac": round(gbs(p) / peak, 4),
                   "GFLOP/s": round(FLOP_NN * vh / (t * 1e-3) / 1e9, 1)} for p, t in times.items()}
@@ -430,8 +432,9 @@ def run_dslash_only():
     fat64 = q.qex_pack_links(lat, "f64", torch.from_numpy(u).cuda())
     fat32 = q.qex_convert_links(lat, "f64", fat64, "f32")
     fatr12 = q.qex_convert_links(lat, "f64", fat64, "f32r12")
+    fatr12h = q.qex_convert_links(lat, "f64", fat64, "f32r12h")
     src = torch.from_numpy(b).cuda()
-    for prec, fat in (("f32r12", fatr12), ("f32", fat32), ("f64", fat64)):
+    for prec, fat in (("f32r12h", fatr12h), ("f32r12", fatr12), ("f32", fat32), ("f64", fat64)):
         inp = q.qex_pack_field(lat, prec, 0, src)
         for _ in range(2):
             out = q.qex_dslash(lat, prec, fat, None, 0.0, 1, inp)
@@ -441,7 +444,7 @@ def run_dslash_only():
 
 SWEEP_L = (8, 12, 16, 24, 32)
 SWEEP_T = (8, 12, 16, 24, 32, 48, 64)
-BYTES_NAIK = {"f64": 2400, "f32": 1200, "f32r12": 1008}  # 16 links (8 two-row fat) + 16 in once + 1 out
+BYTES_NAIK = {"f64": 2400, "f32": 1200, "f32r12": 1008, "f32r12h": 816}  # 16 links + 16 in once + 1 out
 FLOP_NAIK = 1146
 
 
@@ -466,6 +469,7 @@ def run_sweep(args):
         lng64 = torch.randn_like(fat64)
         sets = {"f64": (fat64, lng64), "f32": (fat64.float(), lng64.float())}
         sets["f32r12"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12"), sets["f32"][1])
+        sets["f32r12h"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12h"), sets["f32"][1])
         for prec, (fat, lng) in sets.items():
             inp = q.empty_field(lat, prec).normal_(generator=gen)
             out = q.empty_field(lat, prec)
@@ -505,7 +509,7 @@ def run_sweep(args):
         bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
         x = torch.zeros_like(bh)
         st, stats = q.qex_cg(lat, "f32r12", fat64, lng64, fatr, lng32, -1.0 / 24, wl["mass"], bh, x, tol=TOL,
-                             maxiter=60000, delta=DELTA, check=False)
+                             maxiter=60000, delta=DELTA, check=False)  # Haar at m = 0.005: FP32 two-row inner
         print(json.dumps({"sweep": "cg", "workload": "64^4 Naik, Haar fat links, Gaussian/sqrt(3) long links, "
                           "c3=-1/24, m=0.005", "status": st, **stats}), flush=True)
 

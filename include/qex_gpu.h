@@ -33,11 +33,13 @@
  *            the Vh sites of parity p.  F64: 9 planes of double2 (matrix
  *            element c = 3a+b); F32: 4 planes of float4 (elements 0-1, 2-3,
  *            4-5, 6-7) and 1 plane of float2 (element 8); F32_R12: 3 planes
- *            of float4 (elements 0-1, 2-3, 4-5: rows 0 and 1).  Size
- *            qex_links_bytes().
+ *            of float4 (elements 0-1, 2-3, 4-5: rows 0 and 1); F32_R12H: 1
+ *            plane of 8 int16 (elements 0-3) and 1 plane of 4 int16
+ *            (elements 4-5), re before im.  Size qex_links_bytes().
  *     half field (the Vh sites of one parity): F64: 3 planes of double2
- *            (colour a); F32 and F32_R12: 1 plane of float4 (colours 0,1) +
- *            1 plane of float2 (colour 2).  Size qex_field_bytes().
+ *            (colour a); F32, F32_R12 and F32_R12H: 1 plane of float4
+ *            (colours 0,1) + 1 plane of float2 (colour 2).  Size
+ *            qex_field_bytes().
  * - All field and link pointers are caller-owned DEVICE memory, 16-byte
  *   aligned; the library never frees them.  The library owns only the
  *   lattice object and its scratch (created lazily, freed by destroy).
@@ -75,9 +77,13 @@ typedef enum {
  * their first two rows only (12 reals); the third row is rebuilt in the
  * kernel as the complex conjugate of the cross product of the first two,
  * which is exact for SU(3) matrices only -- use it for unitary, unimodular
- * links.  Long (Naik) links are never compressed: with QEX_F32_R12 the long
- * link set is in QEX_F32 format. */
-typedef enum { QEX_F64 = 0, QEX_F32 = 1, QEX_F32_R12 = 2 } qex_prec;
+ * links.  QEX_F32_R12H is the same with each of the 12 reals stored as a
+ * 16-bit fixed-point number (int16 q, value q / 32767; SU(3) entries lie in
+ * [-1, 1]), quantisation error <= 1.5e-5 per real: an inner-solver format
+ * (use it inside mixed-precision CG, whose FP64 reliable updates correct
+ * it).  Long (Naik) links are never compressed: with QEX_F32_R12 or
+ * QEX_F32_R12H the long link set is in QEX_F32 format. */
+typedef enum { QEX_F64 = 0, QEX_F32 = 1, QEX_F32_R12 = 2, QEX_F32_R12H = 3 } qex_prec;
 
 typedef struct qex_lattice qex_lattice; /* opaque, owned by the library */
 
@@ -226,7 +232,7 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  * ||b - A x|| / ||b|| <= tol, computed in FP64.
  *
  * inner = QEX_F64: plain CG in FP64 on fat64/lng64.
- * inner = QEX_F32 or QEX_F32_R12: mixed precision: the CG iteration runs in
+ * inner = QEX_F32, QEX_F32_R12 or QEX_F32_R12H: mixed precision: the CG iteration runs in
  *   FP32 on fat32/lng32 (fat32 in the `inner` link format, lng32 in QEX_F32;
  *   inner residual and iterate in FP32, all reductions in FP64);
  *   whenever the iterated residual norm drops below delta times its maximum

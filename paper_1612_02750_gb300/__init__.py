@@ -26,9 +26,10 @@ from . import build as _build
 F64 = 0
 F32 = 1
 F32_R12 = 2  # FP32 fields; FP32 SU(3) fat links stored as two rows
-_PREC = {"f64": F64, "f32": F32, "f32r12": F32_R12, F64: F64, F32: F32, F32_R12: F32_R12,
-         torch.float64: F64, torch.float32: F32}
-_DTYPE = {F64: torch.float64, F32: torch.float32, F32_R12: torch.float32}
+F32_R12H = 3  # FP32 fields; SU(3) fat links as two rows of 16-bit fixed point
+_PREC = {"f64": F64, "f32": F32, "f32r12": F32_R12, "f32r12h": F32_R12H, F64: F64, F32: F32, F32_R12: F32_R12,
+         F32_R12H: F32_R12H, torch.float64: F64, torch.float32: F32}
+_DTYPE = {F64: torch.float64, F32: torch.float32, F32_R12: torch.float32, F32_R12H: torch.float32}
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_ALIGN", 4: "ERR_CUDA",
            5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_NAN"}
 

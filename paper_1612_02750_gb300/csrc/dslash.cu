@@ -14,12 +14,14 @@
 
 namespace qex {
 
-// Fat-link formats: 0 = full 3x3 in the field precision, 1 = FP32 two-row
-// (third row rebuilt in registers).
+// Fat-link formats: 0 = full 3x3 in the field precision, 1 = FP32 two-row,
+// 2 = 16-bit fixed-point two-row (third row rebuilt in registers).
 template <typename R, int FMT>
 __device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int mu, int i) {
     if constexpr (FMT == 1)
         return load_link_r12(base, vh, p, mu, i);
+    else if constexpr (FMT == 2)
+        return load_link_r12h(base, vh, p, mu, i);
     else
         return load_link(base, vh, p, mu, i);
 }
@@ -65,7 +67,7 @@ __device__ __forceinline__ Vec3<R> load_in(const DsParams<R> &P, const R *in, si
 }
 
 template <typename R, int FMT, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(const DsParams<R> P) {
+__global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslash_kernel(const DsParams<R> P) {
     __shared__ double smem[32];
     __shared__ unsigned int is_last;
     if (P.check_halt && P.S->halt) return;  // uniform over the grid
@@ -212,12 +214,13 @@ __global__ void __launch_bounds__(kDslashBlock, kDslashMinBlocks) dslash_kernel(
 }
 
 // Grid of a Dslash launch: one thread per site, or, for the variants that end
-// in a grid reduction, a persistent grid of kDslashMinBlocks blocks per SM so
-// that each block pays the reduction's fence-and-atomic tail once.
-static int dslash_grid(const qex_lattice *lat, bool reducing) {
+// in a grid reduction, a persistent grid of as many blocks per SM as the
+// launch bounds keep resident, so that each block pays the reduction's
+// fence-and-atomic tail once.
+static int dslash_grid(const qex_lattice *lat, bool reducing, int min_blocks) {
     const int full = blocks_for(lat->vh, kDslashBlock);
     if (!reducing) return full;
-    const int persistent = sm_count() * kDslashMinBlocks;
+    const int persistent = sm_count() * min_blocks;
     return full < persistent ? full : persistent;
 }
 
@@ -242,7 +245,8 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.psel = a.psel;
     P.partials = lat->partials;
     P.counter = lat->counter;
-    dslash_kernel<R, FMT, NAIK, EPI><<<dslash_grid(lat, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr),
+    dslash_kernel<R, FMT, NAIK, EPI><<<dslash_grid(lat, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr,
+                                                   DslashMinBlocks<R>::value),
                                        kDslashBlock, 0, st>>>(P);
 }
 
@@ -278,6 +282,11 @@ qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st)
                 launch_epi<float, 1, true>(lat, a, st);
             else
                 launch_epi<float, 1, false>(lat, a, st);
+        } else if (a.prec == QEX_F32_R12H) {
+            if (a.lng)
+                launch_epi<float, 2, true>(lat, a, st);
+            else
+                launch_epi<float, 2, false>(lat, a, st);
         } else {
             if (a.lng)
                 launch_epi<float, 0, true>(lat, a, st);

@@ -25,6 +25,8 @@ template <typename R, int FMT>
 __device__ __forceinline__ Mat3<R> load_fat_m(const R *base, size_t vh, int p, int mu, int i) {
     if constexpr (FMT == 1)
         return load_link_r12(base, vh, p, mu, i);
+    else if constexpr (FMT == 2)
+        return load_link_r12h(base, vh, p, mu, i);
     else
         return load_link(base, vh, p, mu, i);
 }
@@ -306,6 +308,11 @@ qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t 
                 launch_m_epi<float, 1, true>(lat, a, st);
             else
                 launch_m_epi<float, 1, false>(lat, a, st);
+        } else if (a.prec == QEX_F32_R12H) {
+            if (a.lng)
+                launch_m_epi<float, 2, true>(lat, a, st);
+            else
+                launch_m_epi<float, 2, false>(lat, a, st);
         } else {
             if (a.lng)
                 launch_m_epi<float, 0, true>(lat, a, st);

@@ -55,7 +55,7 @@ qex_status check_lattice(const qex_lattice *lat) {
 }
 
 qex_status check_prec(qex_prec prec) {
-    if (prec != QEX_F64 && prec != QEX_F32 && prec != QEX_F32_R12) {
+    if (prec != QEX_F64 && prec != QEX_F32 && prec != QEX_F32_R12 && prec != QEX_F32_R12H) {
         set_error("unknown precision %d", (int)prec);
         return QEX_ERR_ARG;
     }
@@ -255,6 +255,7 @@ qex_status qex_neighbor_table_device(const qex_lattice *lat, int parity, int mu,
 size_t qex_links_bytes(const qex_lattice *lat, qex_prec prec) {
     if (!lat) return 0;
     if (prec == QEX_F32_R12) return (size_t)lat->volume * 4 * 12 * 4;
+    if (prec == QEX_F32_R12H) return (size_t)lat->volume * 4 * 12 * 2;
     return (size_t)lat->volume * 4 * 18 * (prec == QEX_F64 ? 8 : 4);
 }
 

@@ -81,6 +81,53 @@ __device__ __forceinline__ void get_link(R12c base, size_t vh, int blk, int i, d
     }
 }
 
+// Two-row links in 16-bit fixed point (q = round(v * 32767), v clamped to
+// [-1, 1]); elements 0..3 in a 16-byte word, 4..5 in an 8-byte word.
+struct R12H {
+    float *p;
+};
+struct R12Hc {
+    const float *p;
+};
+
+__device__ __forceinline__ uint32_t fix16_pair(double re, double im) {
+    const double lo = fmin(1.0, fmax(-1.0, re)), hi = fmin(1.0, fmax(-1.0, im));
+    const int qr = __double2int_rn(lo * 32767.0), qi = __double2int_rn(hi * 32767.0);
+    return (uint32_t)(qr & 0xFFFF) | ((uint32_t)(qi & 0xFFFF) << 16);
+}
+
+__device__ __forceinline__ double fix16_value(uint32_t w, bool hi) {
+    const int16_t q = (int16_t)(hi ? (w >> 16) : (w & 0xFFFFu));
+    return (double)q / 32767.0;
+}
+
+__device__ __forceinline__ void put_link(R12H base, size_t vh, int blk, int i, const double *m) {
+    char *b = reinterpret_cast<char *>(base.p) + (size_t)blk * 24 * vh;
+    reinterpret_cast<uint4 *>(b)[i] = make_uint4(fix16_pair(m[0], m[1]), fix16_pair(m[2], m[3]),
+                                                 fix16_pair(m[4], m[5]), fix16_pair(m[6], m[7]));
+    reinterpret_cast<uint2 *>(b + 16 * vh)[i] = make_uint2(fix16_pair(m[8], m[9]), fix16_pair(m[10], m[11]));
+}
+
+// Reads the two stored rows and rebuilds the third in FP64.
+__device__ __forceinline__ void get_link(R12Hc base, size_t vh, int blk, int i, double *m) {
+    const char *b = reinterpret_cast<const char *>(base.p) + (size_t)blk * 24 * vh;
+    const uint4 a = reinterpret_cast<const uint4 *>(b)[i];
+    const uint2 c = reinterpret_cast<const uint2 *>(b + 16 * vh)[i];
+    const uint32_t w[6] = {a.x, a.y, a.z, a.w, c.x, c.y};
+    Mat3<double> u;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        u.e[k].re = fix16_value(w[k], false);
+        u.e[k].im = fix16_value(w[k], true);
+    }
+    reconstruct_row2(u);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        m[2 * k] = u.e[k].re;
+        m[2 * k + 1] = u.e[k].im;
+    }
+}
+
 __device__ __forceinline__ void put_vec(double *base, size_t vh, int i, const double *v) {
     double2 *b = reinterpret_cast<double2 *>(base) + i;
 #pragma unroll
@@ -200,8 +247,10 @@ static void convert_links_to(qex_prec to, int vh, RI in, void *out, dim3 grid, c
         convert_links_kernel<RI, double *><<<grid, kBlock, 0, s>>>(vh, in, (double *)out);
     else if (to == QEX_F32)
         convert_links_kernel<RI, float *><<<grid, kBlock, 0, s>>>(vh, in, (float *)out);
-    else
+    else if (to == QEX_F32_R12)
         convert_links_kernel<RI, R12><<<grid, kBlock, 0, s>>>(vh, in, R12{(float *)out});
+    else
+        convert_links_kernel<RI, R12H><<<grid, kBlock, 0, s>>>(vh, in, R12H{(float *)out});
 }
 
 }  // namespace qex
@@ -220,8 +269,10 @@ qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *l
         pack_links_kernel<double *><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, (double *)internal);
     else if (prec == QEX_F32)
         pack_links_kernel<float *><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, (float *)internal);
-    else
+    else if (prec == QEX_F32_R12)
         pack_links_kernel<R12><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, R12{(float *)internal});
+    else
+        pack_links_kernel<R12H><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, R12H{(float *)internal});
     QEX_CHECK_LAUNCH("pack_links_kernel");
     return QEX_OK;
 }
@@ -236,8 +287,10 @@ qex_status qex_unpack_links(const qex_lattice *lat, qex_prec prec, const void *i
         unpack_links_kernel<const double *><<<grid, kBlock, 0, s>>>(lat->geom, (const double *)internal, lex_links);
     else if (prec == QEX_F32)
         unpack_links_kernel<const float *><<<grid, kBlock, 0, s>>>(lat->geom, (const float *)internal, lex_links);
-    else
+    else if (prec == QEX_F32_R12)
         unpack_links_kernel<R12c><<<grid, kBlock, 0, s>>>(lat->geom, R12c{(const float *)internal}, lex_links);
+    else
+        unpack_links_kernel<R12Hc><<<grid, kBlock, 0, s>>>(lat->geom, R12Hc{(const float *)internal}, lex_links);
     QEX_CHECK_LAUNCH("unpack_links_kernel");
     return QEX_OK;
 }
@@ -288,8 +341,10 @@ qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *
         convert_links_to<const double *>(to, vh, (const double *)in, out, grid, s);
     else if (from == QEX_F32)
         convert_links_to<const float *>(to, vh, (const float *)in, out, grid, s);
-    else
+    else if (from == QEX_F32_R12)
         convert_links_to<R12c>(to, vh, R12c{(const float *)in}, out, grid, s);
+    else
+        convert_links_to<R12Hc>(to, vh, R12Hc{(const float *)in}, out, grid, s);
     QEX_CHECK_LAUNCH("convert_links_kernel");
     return QEX_OK;
 }

@@ -206,6 +206,34 @@ __device__ __forceinline__ Mat3<float> load_link_r12(const float *base, size_t v
     return m;
 }
 
+// Two-row links in 16-bit fixed point: block (p, mu) holds a plane of 16-byte
+// words (int16 re/im of elements 0..3) then a plane of 8-byte words
+// (elements 4, 5); block size 24*Vh bytes.  value = q / 32767.
+constexpr float kFix16Scale = 1.0f / 32767.0f;
+
+// int16 q in the low (hi = false) or high half of w -> q/32767: the 16 bits,
+// offset by 2^15, become the low mantissa bits of the float 2^23 + 2^15 + q
+// (one LOP3); subtracting 2^23 + 2^15 is exact, so q/32767 is rounded once.
+__device__ __forceinline__ float fix16_half(uint32_t w, bool hi) {
+    const uint32_t u = (hi ? (w >> 16) : (w & 0xFFFFu)) ^ 0x4B008000u;
+    return (__uint_as_float(u) - 8421376.0f) * kFix16Scale;
+}
+
+__device__ __forceinline__ Mat3<float> load_link_r12h(const float *base_f, size_t vh, int p, int mu, int i) {
+    const char *blk = reinterpret_cast<const char *>(base_f) + (size_t)(p * 4 + mu) * 24 * vh;
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(blk) + i);
+    const uint2 b = __ldg(reinterpret_cast<const uint2 *>(blk + 16 * vh) + i);
+    const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    Mat3<float> m;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        m.e[c].re = fix16_half(w[c], false);
+        m.e[c].im = fix16_half(w[c], true);
+    }
+    reconstruct_row2(m);
+    return m;
+}
+
 __device__ __forceinline__ Vec3<double> load_vec(const double *base, size_t vh, int i) {
     const double2 *b = reinterpret_cast<const double2 *>(base) + i;
     Vec3<double> v;
@@ -359,10 +387,16 @@ constexpr int kBlock = 256;  // threads per block of the site kernels
 #define QEX_DSLASH_BLOCK 256
 #endif
 #ifndef QEX_DSLASH_MIN_BLOCKS
-#define QEX_DSLASH_MIN_BLOCKS 3
+#define QEX_DSLASH_MIN_BLOCKS 4
+#endif
+#ifndef QEX_DSLASH_MIN_BLOCKS_F64
+#define QEX_DSLASH_MIN_BLOCKS_F64 3
 #endif
 constexpr int kDslashBlock = QEX_DSLASH_BLOCK;
-constexpr int kDslashMinBlocks = QEX_DSLASH_MIN_BLOCKS;
+constexpr int kDslashMinBlocks = QEX_DSLASH_MIN_BLOCKS;         // FP32 variants
+constexpr int kDslashMinBlocksF64 = QEX_DSLASH_MIN_BLOCKS_F64;  // FP64 variants (ALU bound, no spills)
+template <typename R> struct DslashMinBlocks { static constexpr int value = kDslashMinBlocks; };
+template <> struct DslashMinBlocks<double> { static constexpr int value = kDslashMinBlocksF64; };
 
 inline int blocks_for(int64_t n, int bs = kBlock) { return (int)((n + bs - 1) / bs); }
 

@@ -116,5 +116,6 @@ def test_argument_errors(lib):
     assert lib.qex_field_bytes(h, 1) == 64 * 6 * 4
     assert lib.qex_links_bytes(h, 2) == 4 * 128 * 12 * 4
     assert lib.qex_field_bytes(h, 2) == 64 * 6 * 4
-    assert lib.qex_pack_links(h, 3, None, None, None) == 1  # unknown precision
+    assert lib.qex_links_bytes(h, 3) == 4 * 128 * 12 * 2
+    assert lib.qex_pack_links(h, 4, None, None, None) == 1  # unknown precision
     lib.qex_lattice_destroy(h)

@@ -14,7 +14,8 @@ import fieldgen as fg
 pytestmark = pytest.mark.gpu
 
 C3 = -1.0 / 24.0
-TOL = {"f64": 1e-13, "f32": 1e-5, "f32r12": 1e-5}
+# 16-bit fixed-point links: 1.5e-5 quantisation per real, ~3e-5 per entry of O(0.5)
+TOL = {"f64": 1e-13, "f32": 1e-5, "f32r12": 1e-5, "f32r12h": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -61,11 +62,13 @@ class Setup:
         self.fat["f32"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32")
         if fat in ("haar", "exp", "unit"):  # SU(3) links: two-row storage applies
             self.fat["f32r12"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32r12")
-        self.lng = {"f64": None, "f32": None, "f32r12": None}
+            self.fat["f32r12h"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32r12h")
+        self.lng = {"f64": None, "f32": None, "f32r12": None, "f32r12h": None}
         if naik:
             self.lng["f64"] = q.qex_pack_links(self.lat, "f64", dev(self.w))
             self.lng["f32"] = q.qex_pack_links(self.lat, "f32", dev(self.w))
             self.lng["f32r12"] = self.lng["f32"]  # long links are never compressed
+            self.lng["f32r12h"] = self.lng["f32"]
 
     def half(self, prec, parity, field):
         return self.q.qex_pack_field(self.lat, prec, parity, dev(field))
@@ -126,9 +129,26 @@ def test_two_row_links_roundtrip(q, kind):
     assert np.array_equal(host(via), host(r12))
 
 
+def test_fix16_links_roundtrip(q):
+    """16-bit fixed-point two-row links: rows 0 and 1 come back as
+    round(v * 32767) / 32767, row 2 rebuilt from them; pack and convert agree."""
+    dims = (6, 4, 4, 10)
+    u = fg.random_links(dims, "haar", fg.rng_streams(10)["links"])
+    lat = q.Lattice(dims)
+    h = q.qex_pack_links(lat, "f32r12h", dev(u))
+    assert h.numel() * 4 == q.qex_links_bytes(lat, "f32r12h") == int(np.prod(dims)) * 4 * 12 * 2
+    back = host(q.qex_unpack_links(lat, "f32r12h", h))
+    rows = u[..., :2, :]
+    quant = (np.round(rows.real * 32767) + 1j * np.round(rows.imag * 32767)) / 32767
+    assert np.abs(back[..., :2, :] - quant).max() <= 1e-15
+    assert np.abs(back - u).max() <= 1e-4
+    via = q.qex_convert_links(lat, "f64", q.qex_pack_links(lat, "f64", dev(u)), "f32r12h")
+    assert np.array_equal(host(via).view(np.uint32), host(h).view(np.uint32))  # raw bits (words are not floats)
+
+
 @pytest.mark.parametrize("dims", SHAPES)
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12", "f32r12h"])
 def test_dslash_parity(q, oracle_mod, dims, naik, prec):
     S = Setup(q, dims, naik, seed=21)
     for ap in (True, False):
@@ -154,7 +174,7 @@ def test_dslash_exp_links_and_unit_links(q, oracle_mod):
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12", "f32r12h"])
 def test_normal_op_parity(q, oracle_mod, naik, prec):
     dims = (8, 4, 6, 10)
     S = Setup(q, dims, naik, seed=22)
@@ -192,14 +212,14 @@ def _cg(q, S, inner, m, b_full, tol=1e-10, maxiter=20000, delta=0.1, x0=None):
 
     b = S.half("f64", 0, b_full)
     x = S.half("f64", 0, x0) if x0 is not None else torch.zeros_like(b)
-    f32 = "f32r12" if inner == "f32r12" else "f32"
+    f32 = inner if inner in ("f32r12", "f32r12h") else "f32"
     st, stats = q.qex_cg(S.lat, inner, S.fat["f64"], S.lng["f64"], S.fat[f32], S.lng["f32"], C3, m, b, x,
                          tol=tol, maxiter=maxiter, delta=delta, check=False)
     return st, stats, S.full("f64", 0, x)
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("inner", ["f64", "f32", "f32r12"])
+@pytest.mark.parametrize("inner", ["f64", "f32", "f32r12", "f32r12h"])
 def test_cg_parity(q, oracle_mod, naik, inner):
     dims = (8, 8, 4, 8)
     m = 0.1
