@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--mrhs", action="store_true",
                     help="multi-RHS case: 24^4 Haar links, 16 Gaussian sources, batched Dslash and CG against "
                          "single-RHS calls")
+    ap.add_argument("--batch", action="store_true",
+                    help="multi-lattice case: 8 lattices 8^4 .. 32^4, Haar links, masses 0.005 * 20^(k/7), one "
+                         "batched solve against sequential single-lattice solves")
     ap.add_argument("--dslash-only", action="store_true",
                     help="profiling case: two launches each of the 16-bit two-row, two-row FP32, FP32 and FP64 "
                          "one-hop Dslash on the workload, no timing")
@@ -595,9 +598,62 @@ def run_mrhs(args):
                       "all_converged": all(x["converged"] for x in stm)}), flush=True)
 
 
+BATCH_DIMS = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (20, 20, 20, 20),
+              (24, 24, 24, 24), (24, 24, 24, 48), (32, 32, 32, 32)]
+
+
+def run_batch(args):
+    """Eight independent lattices (Haar links, seed 4 + 10k, masses
+    m_k = 0.005 * 20^(k/7) in the listed order, one Gaussian source each):
+    one qex_cg_batch call against eight qex_cg calls, 16-bit inner links."""
+    import torch
+
+    import fieldgen as fg
+    import paper_1612_02750_gb300 as q
+    from paper_1612_02750_gb300 import build as qbuild
+
+    qbuild.build()
+    q.load()
+    items = []
+    for k, dims in enumerate(BATCH_DIMS):
+        u, _, b = fg.make_inputs(dims, "haar", False, 4 + 10 * k)
+        lat = q.Lattice(dims)
+        fat64 = q.qex_pack_links(lat, "f64", torch.from_numpy(u).cuda())
+        bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
+        items.append({"lat": lat, "fat64": fat64, "fat32": q.qex_convert_links(lat, "f64", fat64, INNER),
+                      "mass": 0.005 * 20 ** (k / 7), "b64": bh, "x64": torch.zeros_like(bh)})
+    delta = 0.1  # Haar links: the robust setting for 16-bit inner links
+    q.qex_cg_batch(items, INNER, tol=TOL, maxiter=400000, delta=delta)  # warm-up (builds scratch)
+    for it in items:
+        it["x64"].zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, stats = q.qex_cg_batch(items, INNER, tol=TOL, maxiter=400000, delta=delta)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    singles = []
+    t0 = time.perf_counter()
+    for it in items:
+        x = torch.zeros_like(it["b64"])
+        _, s1 = q.qex_cg(it["lat"], INNER, it["fat64"], None, it["fat32"], None, 0.0, it["mass"], it["b64"], x,
+                         tol=TOL, maxiter=400000, delta=delta)
+        singles.append(s1)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    print(json.dumps({"batch": "cg", "lattices": ["x".join(map(str, d)) for d in BATCH_DIMS],
+                      "masses": [round(it["mass"], 5) for it in items], "status": st,
+                      "batched_s": round(t_batch, 4), "sequential_s": round(t_seq, 4),
+                      "speedup": round(t_seq / t_batch, 3),
+                      "batched_iters": [x["iters"] for x in stats], "single_iters": [x["iters"] for x in singles],
+                      "max_true_rel_resid": max(x["true_rel_resid"] for x in stats),
+                      "all_converged": all(x["converged"] for x in stats)}), flush=True)
+
+
 def main():
     args = parse()
-    if args.mrhs:
+    if args.batch:
+        run_batch(args)
+    elif args.mrhs:
         run_mrhs(args)
     elif args.sweep:
         run_sweep(args)

@@ -284,6 +284,39 @@ qex_status qex_cg_mrhs(const qex_lattice *lat, qex_prec inner, const void *fat64
                        const void *fat32, const void *lng32, double c_naik, double mass, int nrhs, const void *b64,
                        void *x64, double tol, int maxiter, double delta, void *stream, qex_cg_stats *stats);
 
+/* Largest number of lattices in one qex_cg_batch call. */
+#define QEX_BATCH_MAX 64
+
+/* One problem of a batched solve: its own lattice object (not shared with
+ * another item), links, mass, source and solution.  fat64/lng64: F64 link
+ * sets; fat32/lng32: the inner-precision copies (fat32 in the `inner` link
+ * format, lng32 in QEX_F32) when inner != QEX_F64; lng64 NULL = no Naik
+ * term (all items of a batch agree).  b64, x64: F64 even half fields, x64
+ * holding the initial guess. */
+typedef struct {
+    const qex_lattice *lat;
+    const void *fat64, *lng64;
+    const void *fat32, *lng32;
+    double c_naik;
+    double mass;
+    const void *b64;
+    void *x64;
+} qex_cg_item;
+
+/* Batched CG over n independent lattices (different extents, links and
+ * masses): every kernel of an iteration is one launch over a work list of
+ * (lattice, 256-site tile) items of all running lattices, so small lattices
+ * share the GPU.  Each lattice has its own alpha, beta, residual norms,
+ * reliable updates and FP64 true-residual stop (tol, maxiter and delta are
+ * common); the lattices iterate in lockstep and a converged one stops.  The
+ * scratch of the batch (descriptors, scalars, per-tile partials) is owned by
+ * items[0].lat; the CG vectors of each item live in its own lattice's work
+ * area.  stats (may be NULL) receives n entries.  Synchronises the stream.
+ * Errors as qex_cg; QEX_ERR_ARG also for 0 or more than QEX_BATCH_MAX items,
+ * items sharing a lattice object, or items disagreeing on the Naik term. */
+qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inner, double tol, int maxiter, double delta,
+                        void *stream, qex_cg_stats *stats);
+
 /* End-to-end solve from HOST memory (the call for users whose fields live
  * on the host).  host_fat (and host_lng, or NULL) are canonical complex-double
  * links [V][4][3][3]; host_b is a canonical complex-double field [V][3] whose

@@ -42,6 +42,12 @@ class QexError(RuntimeError):
         self.status = status
 
 
+class CgItem(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_void_p), ("fat64", ctypes.c_void_p), ("lng64", ctypes.c_void_p),
+                ("fat32", ctypes.c_void_p), ("lng32", ctypes.c_void_p), ("c_naik", ctypes.c_double),
+                ("mass", ctypes.c_double), ("b64", ctypes.c_void_p), ("x64", ctypes.c_void_p)]
+
+
 class CgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
                 ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
@@ -89,6 +95,7 @@ def load():
         "qex_force": (i, [vp, vp, vp, d, vp, vp, i, vp, vp, vp]),
         "qex_dslash_mrhs": (i, [vp, i, vp, vp, d, i, i, vp, vp, vp]),
         "qex_cg_mrhs": (i, [vp, i, vp, vp, vp, vp, d, d, i, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_cg_batch": (i, [i, ctypes.POINTER(CgItem), i, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -107,8 +114,8 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_launch_count", "qex_last_error",
-            "qex_version"]
+            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_launch_count",
+            "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -451,6 +458,30 @@ def qex_cg_mrhs(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, 
     if check:
         _check(st)
     return st, [stats[k].as_dict() for k in range(int(nrhs))]
+
+
+def qex_cg_batch(items, inner, tol: float = 1e-10, maxiter: int = 100000, delta: float = 0.1, stream=None,
+                 check: bool = True):
+    """Batched solve over independent lattices.  ``items`` is a list of dicts
+    with keys lat, fat64, lng64, fat32, lng32, c_naik, mass, b64, x64 (x64 is
+    overwritten).  Returns (status, list of per-item stats dicts)."""
+    n = len(items)
+    arr = (CgItem * n)()
+    for k, it in enumerate(items):
+        arr[k].lat = it["lat"].handle
+        arr[k].fat64 = _ptr(it["fat64"])
+        arr[k].lng64 = _ptr(it.get("lng64"))
+        arr[k].fat32 = _ptr(it.get("fat32"))
+        arr[k].lng32 = _ptr(it.get("lng32"))
+        arr[k].c_naik = float(it.get("c_naik", 0.0))
+        arr[k].mass = float(it["mass"])
+        arr[k].b64 = _ptr(it["b64"])
+        arr[k].x64 = _ptr(it["x64"])
+    stats = (CgStats * n)()
+    st = load().qex_cg_batch(n, arr, _prec(inner), float(tol), int(maxiter), float(delta), _stream(stream), stats)
+    if check:
+        _check(st)
+    return st, [stats[k].as_dict() for k in range(n)]
 
 
 def qex_last_error() -> str:

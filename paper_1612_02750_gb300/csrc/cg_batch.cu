@@ -1,0 +1,585 @@
+// cg_batch.cu -- conjugate gradient on many independent lattices at once
+// (different extents, masses and links), each launch covering a work list of
+// (lattice, 256-site tile) items.
+//
+// Small lattices cannot fill the GPU on their own; batching them makes every
+// kernel of an iteration one launch over the tiles of all running lattices.
+// Each lattice keeps its own alpha, beta, norms and reliable-update state;
+// the lattices iterate in lockstep (the lockstep count's parity selects the
+// direction buffers), a lattice whose FP64 true residual meets tol stops
+// (its tiles return at once), and a reliable update requested by some
+// lattices is done for exactly those.  Reductions are per tile, summed per
+// lattice in tile order by the last block (bit-reproducible).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "qex_dslash_site.cuh"
+#include "qex_kernels.cuh"
+
+namespace qex {
+
+constexpr int kTile = 256;  // sites per tile (one block)
+
+struct LatDesc {
+    Geom g;
+    int tile0, ntiles;
+    const void *fat_in, *lng_in;  // inner-precision links
+    const double *fat64, *lng64;
+    const double *b;
+    double *x64, *r64, *tmp64;
+    void *xi, *ri, *p0, *p1, *api, *tmpi;  // inner-precision CG vectors
+    double m2, c3;
+};
+
+struct BatchScalars {
+    double rr[kMaxRhs], pAp[kMaxRhs], alpha[kMaxRhs], beta[kMaxRhs], bb[kMaxRhs], stop2[kMaxRhs],
+        rmax2[kMaxRhs], true_rr[kMaxRhs];
+    int active[kMaxRhs], done[kMaxRhs], need[kMaxRhs], iters[kMaxRhs];
+    double tol2, delta2;
+    int n, iter, maxiter, halt, error, any_need, nactive, reliable_updates;
+};
+
+enum BatchRole {
+    ROLE_K1 = 0,   // tmp = D_oe (r + beta p_old), p_new stored          (inner, running lattices)
+    ROLE_K2 = 1,   // ap = m^2 p_new - D_eo tmp, <p_new, ap> -> alpha    (inner, running lattices)
+    ROLE_RU1 = 2,  // tmp64 = D_oe x64                                   (FP64, lattices in a reliable update)
+    ROLE_RU2 = 3   // r64 = b - m^2 x64 + D_eo tmp64, ||r64||^2 -> flags (FP64, lattices in a reliable update)
+};
+
+__device__ __forceinline__ int lattice_of_tile(const LatDesc *d, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {  // last lattice with tile0 <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-tile partial -> partials[t]; the last block sums each lattice's tiles
+// in order (one warp per lattice).  Returns true in the last block; the
+// per-lattice totals are then in tot[] (shared).
+__device__ __forceinline__ bool batch_reduce(double part, double *partials, unsigned int *counter, int n,
+                                             const LatDesc *d, double *smem, double *tot) {
+    __shared__ unsigned int is_last;
+    const double bs = block_sum(part, smem);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = bs;
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int l = warp; l < n; l += nw) {
+        double v = 0.0;
+        for (int k = lane; k < d[l].ntiles; k += 32) v += __ldcg(partials + d[l].tile0 + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) tot[l] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+template <typename R, int FMT, bool NAIK, int ROLE>
+__global__ void __launch_bounds__(kTile, 3)
+batch_dslash_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, double *partials,
+                    unsigned int *counter) {
+    __shared__ double smem[32];
+    __shared__ double tot[kMaxRhs];
+    if ((ROLE == ROLE_K1 || ROLE == ROLE_K2) && S->halt) return;  // uniform over the grid
+    const int l = lattice_of_tile(descs, n, blockIdx.x);
+    const LatDesc &D = descs[l];
+    const bool fp64 = ROLE == ROLE_RU1 || ROLE == ROLE_RU2;
+    const bool run = fp64 ? S->need[l] != 0 : S->active[l] != 0;  // uniform over the block
+    const int p = (ROLE == ROLE_K1 || ROLE == ROLE_RU1) ? 1 : 0;
+    const Geom &g = D.g;
+    const size_t vh = (size_t)g.vh;
+    const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
+    const int it = S->iter;
+    const R *pold = (const R *)((it & 1) ? D.p1 : D.p0);
+    R *pnew = (R *)((it & 1) ? D.p0 : D.p1);
+    double part = 0.0;
+    if (run && i < g.vh) {
+        const Site s = site_of(g, p, i);
+        if constexpr (ROLE == ROLE_K1) {
+            const R beta = (R)S->beta[l];
+            const R *r = (const R *)D.ri;
+            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, (const R *)D.fat_in, (const R *)D.lng_in, (R)D.c3, p, i,
+                                                          s, [&](int j) { return axpy_vec(r, pold, beta, vh, j); });
+            store_vec((R *)D.tmpi, vh, i, acc);
+            store_vec(pnew, vh, i, axpy_vec(r, pold, beta, vh, i));
+        } else if constexpr (ROLE == ROLE_K2) {
+            const R *tmp = (const R *)D.tmpi;
+            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, (const R *)D.fat_in, (const R *)D.lng_in, (R)D.c3, p, i,
+                                                          s, [&](int j) { return load_vec(tmp, vh, j); });
+            const Vec3<R> qv = load_vec((const R *)pnew, vh, i);
+            const R m2 = (R)D.m2;
+            Vec3<R> o;
+            R dd = R(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = fma(m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = fma(m2, qv.c[a].im, -acc.c[a].im);
+                dd = fma(qv.c[a].re, o.c[a].re, dd);
+                dd = fma(qv.c[a].im, o.c[a].im, dd);
+            }
+            store_vec((R *)D.api, vh, i, o);
+            part = (double)dd;
+        } else if constexpr (ROLE == ROLE_RU1) {
+            const double *x = D.x64;
+            const Vec3<double> acc = dslash_site<double, 0, NAIK>(g, D.fat64, D.lng64, D.c3, p, i, s,
+                                                                  [&](int j) { return load_vec(x, vh, j); });
+            store_vec(D.tmp64, vh, i, acc);
+        } else {
+            const double *tmp = D.tmp64;
+            const Vec3<double> acc = dslash_site<double, 0, NAIK>(g, D.fat64, D.lng64, D.c3, p, i, s,
+                                                                  [&](int j) { return load_vec(tmp, vh, j); });
+            const Vec3<double> xv = load_vec(D.x64, vh, i), bv = load_vec(D.b, vh, i);
+            Vec3<double> o;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = bv.c[a].re - fma(D.m2, xv.c[a].re, -acc.c[a].re);
+                o.c[a].im = bv.c[a].im - fma(D.m2, xv.c[a].im, -acc.c[a].im);
+                part = fma(o.c[a].re, o.c[a].re, part);
+                part = fma(o.c[a].im, o.c[a].im, part);
+            }
+            store_vec(D.r64, vh, i, o);
+        }
+    }
+    if constexpr (ROLE == ROLE_K1 || ROLE == ROLE_RU1) {
+        return;
+    } else {
+        if (!batch_reduce(part, partials, counter, n, descs, smem, tot)) return;
+        if (threadIdx.x != 0) return;
+        for (int k = 0; k < n; ++k) {
+            const double v = tot[k];
+            if constexpr (ROLE == ROLE_K2) {
+                if (!S->active[k]) continue;
+                S->pAp[k] = v;
+                if (!(v > 0.0) || !isfinite(v)) {
+                    S->error = isfinite(v) ? 2 : 1;
+                    S->halt = 1;
+                } else {
+                    S->alpha[k] = S->rr[k] / v;
+                }
+            } else {
+                if (!S->need[k]) continue;
+                S->need[k] = 0;
+                S->true_rr[k] = v;
+                if (!isfinite(v)) {
+                    S->error = 1;
+                    continue;
+                }
+                S->beta[k] = S->rr[k] > 0.0 ? v / S->rr[k] : 0.0;
+                S->rr[k] = v;
+                S->rmax2[k] = v;
+                if (v <= S->stop2[k]) {
+                    S->done[k] = 1;
+                    S->active[k] = 0;
+                }
+            }
+        }
+        if constexpr (ROLE == ROLE_RU2) {
+            int na = 0;
+            for (int k = 0; k < n; ++k) na += S->active[k];
+            S->nactive = na;
+            S->any_need = 0;
+            S->reliable_updates += 1;
+            S->halt = (na == 0 || S->iter >= S->maxiter || S->error) ? 1 : 0;
+        }
+    }
+}
+
+// x += alpha p_new; r -= alpha ap; ||r||^2 per lattice, then the decisions.
+template <typename R>
+__global__ void __launch_bounds__(kTile)
+batch_update_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, double *partials,
+                    unsigned int *counter) {
+    __shared__ double smem[32];
+    __shared__ double tot[kMaxRhs];
+    if (S->halt) return;
+    const int l = lattice_of_tile(descs, n, blockIdx.x);
+    const LatDesc &D = descs[l];
+    const size_t vh = (size_t)D.g.vh;
+    const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
+    double part = 0.0;
+    if (S->active[l] && i < D.g.vh) {
+        const R alpha = (R)S->alpha[l];
+        const R *p = (const R *)((S->iter & 1) ? D.p0 : D.p1);
+        R *x = (R *)D.xi, *r = (R *)D.ri;
+        Vec3<R> xv = load_vec(x, vh, i), rv = load_vec(r, vh, i);
+        const Vec3<R> pv = load_vec(p, vh, i), av = load_vec((const R *)D.api, vh, i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
+            xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
+            rv.c[a].re = fma(-alpha, av.c[a].re, rv.c[a].re);
+            rv.c[a].im = fma(-alpha, av.c[a].im, rv.c[a].im);
+            part += (double)(rv.c[a].re * rv.c[a].re + rv.c[a].im * rv.c[a].im);
+        }
+        store_vec(x, vh, i, xv);
+        store_vec(r, vh, i, rv);
+    }
+    if (!batch_reduce(part, partials, counter, n, descs, smem, tot)) return;
+    if (threadIdx.x != 0) return;
+    S->iter += 1;
+    int any = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!S->active[k]) continue;
+        const double v = tot[k];
+        S->iters[k] += 1;
+        if (!isfinite(v)) {
+            S->error = 1;
+            continue;
+        }
+        if (v > S->rmax2[k]) S->rmax2[k] = v;
+        if (v <= S->stop2[k] || v < S->delta2 * S->rmax2[k] || S->iter >= S->maxiter) {
+            S->need[k] = 1;  // rr keeps its old value: beta comes from the true residual
+            any = 1;
+        } else {
+            S->beta[k] = v / S->rr[k];
+            S->rr[k] = v;
+        }
+    }
+    S->any_need = any;
+    S->halt = (any || S->error) ? 1 : 0;
+}
+
+// Reliable-update helpers over the lattices with need set (mixed precision):
+// x64 += xh, xh = 0 before the FP64 residual; r_inner = (float) r64 after it.
+template <bool ACCUM>
+__global__ void __launch_bounds__(kTile)
+batch_ru_vectors_kernel(const LatDesc *__restrict__ descs, int n, const BatchScalars *S, const int *need_snapshot) {
+    const int l = lattice_of_tile(descs, n, blockIdx.x);
+    if (!need_snapshot[l]) return;
+    const LatDesc &D = descs[l];
+    const size_t vh = (size_t)D.g.vh;
+    const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
+    if (i >= D.g.vh) return;
+    if (ACCUM) {
+        Vec3<double> xv = load_vec(D.x64, vh, i);
+        const Vec3<float> hv = load_vec((const float *)D.xi, vh, i);
+        Vec3<float> z;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xv.c[a].re += (double)hv.c[a].re;
+            xv.c[a].im += (double)hv.c[a].im;
+            z.c[a].re = z.c[a].im = 0.f;
+        }
+        store_vec(D.x64, vh, i, xv);
+        store_vec((float *)D.xi, vh, i, z);
+    } else {
+        const Vec3<double> rd = load_vec(D.r64, vh, i);
+        Vec3<float> rv;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            rv.c[a].re = (float)rd.c[a].re;
+            rv.c[a].im = (float)rd.c[a].im;
+        }
+        store_vec((float *)D.ri, vh, i, rv);
+    }
+}
+
+// ||b||^2 per lattice (stop criterion); zero sources are solved (x = 0).
+__global__ void __launch_bounds__(kTile)
+batch_norm2_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, double *partials,
+                   unsigned int *counter) {
+    __shared__ double smem[32];
+    __shared__ double tot[kMaxRhs];
+    const int l = lattice_of_tile(descs, n, blockIdx.x);
+    const LatDesc &D = descs[l];
+    const size_t vh = (size_t)D.g.vh;
+    const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
+    double part = 0.0;
+    if (i < D.g.vh) {
+        const Vec3<double> v = load_vec(D.b, vh, i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) part += v.c[a].re * v.c[a].re + v.c[a].im * v.c[a].im;
+    }
+    if (!batch_reduce(part, partials, counter, n, descs, smem, tot)) return;
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < n; ++k) {
+        S->bb[k] = tot[k];
+        S->stop2[k] = S->tol2 * tot[k];
+        if (!isfinite(tot[k])) S->error = 1;
+        S->need[k] = 1;  // the first FP64 residual
+        if (tot[k] == 0.0) {
+            S->active[k] = 0;
+            S->done[k] = 1;
+            S->need[k] = 0;
+        }
+    }
+}
+
+// Batch scratch, owned by the first item's lattice.
+struct BatchCtx {
+    LatDesc *descs;
+    BatchScalars *S;
+    BatchScalars *host;
+    int *need_snap;
+    double *partials;
+    unsigned int *counter;
+    int cap_lat, cap_tiles;
+};
+
+void free_batch_ctx(void *p) {
+    BatchCtx *c = (BatchCtx *)p;
+    if (!c) return;
+    cudaFree(c->descs);
+    cudaFree(c->S);
+    cudaFreeHost(c->host);
+    cudaFree(c->need_snap);
+    cudaFree(c->partials);
+    cudaFree(c->counter);
+    delete c;
+}
+
+static size_t al256b(size_t n) { return (n + 255) & ~size_t(255); }
+
+qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
+                             const void *in, const void *out);
+
+template <typename R, int FMT, bool NAIK>
+static void launch_role(int role, int ntiles, const BatchCtx *c, int n, cudaStream_t s) {
+    if (role == ROLE_K1)
+        batch_dslash_kernel<R, FMT, NAIK, ROLE_K1><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+    else if (role == ROLE_K2)
+        batch_dslash_kernel<R, FMT, NAIK, ROLE_K2><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+    else if (role == ROLE_RU1)
+        batch_dslash_kernel<R, FMT, NAIK, ROLE_RU1><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+    else
+        batch_dslash_kernel<R, FMT, NAIK, ROLE_RU2><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+}
+
+template <typename R, int FMT>
+static void launch_role_naik(bool naik, int role, int ntiles, const BatchCtx *c, int n, cudaStream_t s) {
+    if (naik)
+        launch_role<R, FMT, true>(role, ntiles, c, n, s);
+    else
+        launch_role<R, FMT, false>(role, ntiles, c, n, s);
+}
+
+static void launch_batch_dslash(qex_prec inner, bool naik, int role, int ntiles, const BatchCtx *c, int n,
+                                cudaStream_t s) {
+    if (inner == QEX_F64)
+        launch_role_naik<double, 0>(naik, role, ntiles, c, n, s);
+    else if (inner == QEX_F32_R12)
+        launch_role_naik<float, 1>(naik, role, ntiles, c, n, s);
+    else if (inner == QEX_F32_R12H)
+        launch_role_naik<float, 2>(naik, role, ntiles, c, n, s);
+    else
+        launch_role_naik<float, 0>(naik, role, ntiles, c, n, s);
+}
+
+}  // namespace qex
+
+using namespace qex;
+
+extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inner, double tol, int maxiter,
+                                   double delta, void *stream, qex_cg_stats *stats) {
+    qex_status st;
+    if (n < 1 || n > QEX_BATCH_MAX || !items) {
+        set_error("need 1 <= n <= %d items", QEX_BATCH_MAX);
+        return QEX_ERR_ARG;
+    }
+    if ((st = check_prec(inner))) return st;
+    if (!(tol > 0.0) || maxiter < 0 || !(delta >= 0.0 && delta < 1.0)) {
+        set_error("need tol > 0, maxiter >= 0 and 0 <= delta < 1");
+        return QEX_ERR_ARG;
+    }
+    const bool mixed = inner != QEX_F64;
+    const bool naik = items[0].lng64 != nullptr;
+    int total_tiles = 0;
+    for (int k = 0; k < n; ++k) {
+        const qex_cg_item &it = items[k];
+        if ((st = check_dslash_args(it.lat, QEX_F64, it.fat64, it.lng64, it.b64, it.x64))) return st;
+        if ((it.lng64 != nullptr) != naik) {
+            set_error("all batch items must agree on the Naik term");
+            return QEX_ERR_ARG;
+        }
+        if (mixed && (!it.fat32 || !aligned16(it.fat32) || (naik && (!it.lng32 || !aligned16(it.lng32))))) {
+            set_error("item %d: mixed precision needs aligned inner-precision links", k);
+            return QEX_ERR_ARG;
+        }
+        for (int j = 0; j < k; ++j)
+            if (items[j].lat == it.lat) {
+                set_error("items %d and %d share a lattice object (each needs its own work vectors)", j, k);
+                return QEX_ERR_ARG;
+            }
+        total_tiles += blocks_for(it.lat->vh, kTile);
+    }
+    const cudaStream_t s = as_stream(stream);
+    qex_lattice *own = const_cast<qex_lattice *>(items[0].lat);
+
+    // per-lattice work vectors in each lattice's own work area
+    std::vector<LatDesc> descs(n);
+    int tile = 0;
+    for (int k = 0; k < n; ++k) {
+        const qex_cg_item &it = items[k];
+        qex_lattice *lat = const_cast<qex_lattice *>(it.lat);
+        const size_t f64 = al256b((size_t)lat->vh * 48), fi = al256b((size_t)lat->vh * (mixed ? 24 : 48));
+        if ((st = ensure_work(lat, 2 * f64 + 6 * fi))) return st;
+        char *w = (char *)lat->work;
+        LatDesc &D = descs[k];
+        memset(&D, 0, sizeof(D));
+        D.g = lat->geom;
+        D.tile0 = tile;
+        D.ntiles = blocks_for(lat->vh, kTile);
+        tile += D.ntiles;
+        D.fat_in = mixed ? it.fat32 : it.fat64;
+        D.lng_in = mixed ? it.lng32 : it.lng64;
+        D.fat64 = (const double *)it.fat64;
+        D.lng64 = (const double *)it.lng64;
+        D.b = (const double *)it.b64;
+        D.x64 = (double *)it.x64;
+        D.r64 = (double *)w;
+        w += f64;
+        D.tmp64 = (double *)w;
+        w += f64;
+        if (mixed) {
+            D.xi = w;
+            w += fi;
+            D.ri = w;
+            w += fi;
+        } else {
+            D.xi = D.x64;
+            D.ri = D.r64;
+            w += 2 * fi;
+        }
+        D.p0 = w;
+        w += fi;
+        D.p1 = w;
+        w += fi;
+        D.api = w;
+        w += fi;
+        D.tmpi = mixed ? (void *)w : (void *)D.tmp64;
+        D.m2 = it.mass * it.mass;
+        D.c3 = it.c_naik;
+    }
+
+    // batch scratch on the first lattice
+    BatchCtx *c = (BatchCtx *)own->batch_ctx;
+    if (!c || c->cap_lat < n || c->cap_tiles < total_tiles) {
+        if (c) {
+            QEX_CUDA(cudaStreamSynchronize(s));
+            free_batch_ctx(c);
+            own->batch_ctx = nullptr;
+        }
+        c = new BatchCtx;
+        memset(c, 0, sizeof(*c));
+        c->cap_lat = QEX_BATCH_MAX;
+        c->cap_tiles = total_tiles;
+        QEX_CUDA(cudaMalloc(&c->descs, sizeof(LatDesc) * QEX_BATCH_MAX));
+        QEX_CUDA(cudaMalloc(&c->S, sizeof(BatchScalars)));
+        QEX_CUDA(cudaMallocHost(&c->host, sizeof(BatchScalars)));
+        QEX_CUDA(cudaMalloc(&c->need_snap, sizeof(int) * QEX_BATCH_MAX));
+        QEX_CUDA(cudaMalloc(&c->partials, sizeof(double) * total_tiles));
+        QEX_CUDA(cudaMalloc(&c->counter, sizeof(unsigned int)));
+        QEX_CUDA(cudaMemset(c->counter, 0, sizeof(unsigned int)));
+        own->batch_ctx = c;
+    }
+    QEX_CUDA(cudaStreamSynchronize(s));  // the pinned slot is free
+    BatchScalars *h = c->host;
+    memset(h, 0, sizeof(*h));
+    h->n = n;
+    h->tol2 = tol * tol;
+    h->delta2 = mixed ? delta * delta : 0.0;
+    h->maxiter = maxiter;
+    for (int k = 0; k < n; ++k) h->active[k] = 1;
+    cudaEvent_t t0, t1;
+    QEX_CUDA(cudaEventCreate(&t0));
+    QEX_CUDA(cudaEventCreate(&t1));
+    QEX_CUDA(cudaEventRecord(t0, s));
+    QEX_CUDA(cudaMemcpyAsync(c->descs, descs.data(), sizeof(LatDesc) * n, cudaMemcpyHostToDevice, s));
+    QEX_CUDA(cudaMemcpyAsync(c->S, h, sizeof(BatchScalars), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < n; ++k) {
+        const size_t fb = (size_t)items[k].lat->vh * (mixed ? 24 : 48);
+        QEX_CUDA(cudaMemsetAsync(descs[k].p0, 0, fb, s));
+        QEX_CUDA(cudaMemsetAsync(descs[k].p1, 0, fb, s));
+        if (mixed) QEX_CUDA(cudaMemsetAsync(descs[k].xi, 0, fb, s));
+    }
+    batch_norm2_kernel<<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+    QEX_CHECK_LAUNCH("batch_norm2_kernel");
+
+    auto reliable_update = [&]() -> qex_status {
+        // lattices in the update: snapshot of need (the residual kernel clears it)
+        QEX_CUDA(cudaMemcpyAsync(c->need_snap, c->S->need, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+        if (mixed) {
+            batch_ru_vectors_kernel<true><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->need_snap);
+            QEX_CHECK_LAUNCH("batch_ru_vectors_kernel");
+        }
+        launch_batch_dslash(QEX_F64, naik, ROLE_RU1, total_tiles, c, n, s);
+        QEX_CHECK_LAUNCH("batch_dslash_kernel");
+        launch_batch_dslash(QEX_F64, naik, ROLE_RU2, total_tiles, c, n, s);
+        QEX_CHECK_LAUNCH("batch_dslash_kernel");
+        if (mixed) {
+            batch_ru_vectors_kernel<false><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->need_snap);
+            QEX_CHECK_LAUNCH("batch_ru_vectors_kernel");
+        }
+        return QEX_OK;
+    };
+    auto iteration = [&]() -> qex_status {
+        launch_batch_dslash(inner, naik, ROLE_K1, total_tiles, c, n, s);
+        QEX_CHECK_LAUNCH("batch_dslash_kernel");
+        launch_batch_dslash(inner, naik, ROLE_K2, total_tiles, c, n, s);
+        QEX_CHECK_LAUNCH("batch_dslash_kernel");
+        if (mixed)
+            batch_update_kernel<float><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+        else
+            batch_update_kernel<double><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+        QEX_CHECK_LAUNCH("batch_update_kernel");
+        return QEX_OK;
+    };
+    auto fetch = [&]() -> qex_status {
+        QEX_CUDA(cudaMemcpyAsync(h, c->S, sizeof(BatchScalars), cudaMemcpyDeviceToHost, s));
+        QEX_CUDA(cudaStreamSynchronize(s));
+        return QEX_OK;
+    };
+
+    if ((st = reliable_update()) || (st = fetch())) return st;
+    for (int k = 0; k < n; ++k)  // zero sources: x = 0 exactly
+        if (h->bb[k] == 0.0) QEX_CUDA(cudaMemsetAsync(items[k].x64, 0, (size_t)items[k].lat->vh * 48, s));
+    const int batch = 8;
+    while (!st && !h->error && !h->halt) {
+        for (int k = 0; k < batch && !st; ++k) st = iteration();
+        if (st || (st = fetch())) break;
+        if (h->error || !h->any_need) continue;
+        if ((st = reliable_update()) || (st = fetch())) break;
+    }
+    if (st) return st;
+    QEX_CUDA(cudaEventRecord(t1, s));
+    QEX_CUDA(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    int all = 1;
+    for (int k = 0; k < n; ++k) all &= h->done[k];
+    qex_status result = QEX_OK;
+    if (h->error) {
+        set_error("NaN/Inf or CG breakdown in a batched solve");
+        result = QEX_ERR_NAN;
+    } else if (!all) {
+        set_error("batched CG: not every lattice converged in %d iterations", maxiter);
+        result = QEX_ERR_NOT_CONVERGED;
+    }
+    if (stats)
+        for (int k = 0; k < n; ++k) {
+            stats[k].iters = h->iters[k];
+            stats[k].reliable_updates = h->reliable_updates > 0 ? h->reliable_updates - 1 : 0;
+            stats[k].converged = h->done[k];
+            stats[k].reserved = 0;
+            stats[k].true_rel_resid = h->bb[k] > 0.0 ? sqrt(h->true_rr[k] / h->bb[k]) : 0.0;
+            stats[k].time_ms = ms;
+        }
+    return result;
+}

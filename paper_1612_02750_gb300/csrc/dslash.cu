@@ -10,21 +10,10 @@
 // is folded into the links.
 #include <type_traits>
 
+#include "qex_dslash_site.cuh"
 #include "qex_kernels.cuh"
 
 namespace qex {
-
-// Fat-link formats: 0 = full 3x3 in the field precision, 1 = FP32 two-row,
-// 2 = 16-bit fixed-point two-row (third row rebuilt in registers).
-template <typename R, int FMT>
-__device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int mu, int i) {
-    if constexpr (FMT == 1)
-        return load_link_r12(base, vh, p, mu, i);
-    else if constexpr (FMT == 2)
-        return load_link_r12h(base, vh, p, mu, i);
-    else
-        return load_link(base, vh, p, mu, i);
-}
 
 template <typename R>
 struct DsParams {
@@ -46,25 +35,6 @@ struct DsParams {
     double *partials;
     unsigned int *counter;
 };
-
-// Input colour vector at index j: the field itself, or (EPI_PUPD) the new
-// search direction r + beta p_old formed on the fly.
-template <typename R, int EPI>
-__device__ __forceinline__ Vec3<R> load_in(const DsParams<R> &P, const R *in, size_t vh, int j, const R *pold,
-                                           R beta) {
-    if constexpr (EPI == EPI_PUPD) {
-        const Vec3<R> rv = load_vec(P.r, vh, j), pv = load_vec(pold, vh, j);
-        Vec3<R> v;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            v.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
-            v.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
-        }
-        return v;
-    } else {
-        return load_vec(in, vh, j);
-    }
-}
 
 template <typename R, int FMT, bool NAIK, int EPI>
 __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslash_kernel(const DsParams<R> P) {
@@ -92,46 +62,18 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     // the lattice, several when the launch is persistent (reducing variants)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += gridDim.x * blockDim.x) {
         const Site s = site_of(g, p, i);
-        Vec3<R> acc;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = R(0);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const R eta = eta_bit(s, mu) ? R(-1) : R(1);
-            {   // + eta b U_mu(x) psi(x + mu)
-                const int j = hop_index(g, s, mu, 1);
-                const Mat3<R> u = load_fat<R, FMT>(P.fat, vh, p, mu, i);
-                const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
-                acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, v);
-            }
-            {   // - eta b U_mu(x - mu)^+ psi(x - mu)
-                const int j = hop_index(g, s, mu, -1);
-                const Mat3<R> u = load_fat<R, FMT>(P.fat, vh, 1 - p, mu, j);
-                const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
-                acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, v);
-            }
-            if (NAIK) {
-                const R e3 = P.c3 * eta;
-                {
-                    const int j = hop_index(g, s, mu, 3);
-                    const Mat3<R> u = load_link(P.lng, vh, p, mu, i);
-                    const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
-                    acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, v);
-                }
-                {
-                    const int j = hop_index(g, s, mu, -3);
-                    const Mat3<R> u = load_link(P.lng, vh, 1 - p, mu, j);
-                    const Vec3<R> v = load_in<R, EPI>(P, in, vh, j, pold, beta);
-                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, v);
-                }
-            }
-        }
+        const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, P.fat, P.lng, P.c3, p, i, s, [&](int j) {
+            if constexpr (EPI == EPI_PUPD)
+                return axpy_vec(P.r, pold, beta, vh, j);
+            else
+                return load_vec(in, vh, j);
+        });
         if constexpr (EPI == EPI_PLAIN) {
             store_vec(P.out, vh, i, acc);
         } else if constexpr (EPI == EPI_PUPD) {
             store_vec(P.out, vh, i, acc);
             // this thread also owns index i of the other parity's direction
-            store_vec(pnew, vh, i, load_in<R, EPI>(P, in, vh, i, pold, beta));
+            store_vec(pnew, vh, i, axpy_vec(P.r, pold, beta, vh, i));
         } else if constexpr (EPI == EPI_NORMAL) {
             // out = m^2 q - D in;  part = Re <q, out>
             const R *q = P.q;

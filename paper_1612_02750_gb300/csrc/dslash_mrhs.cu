@@ -7,6 +7,7 @@
 // per right-hand side, the input vector once and the output once.  The
 // reducing epilogues run a persistent grid-stride loop and reduce per
 // right-hand side in a fixed order (bit-reproducible).
+#include "qex_dslash_site.cuh"
 #include "qex_kernels.cuh"
 
 namespace qex {
@@ -20,16 +21,6 @@ namespace qex {
 constexpr int kMrhsGroup = 4;                  // right-hand sides per site within a warp
 constexpr int kMrhsBlock = 256;                // threads per block
 constexpr int kMrhsSitesPerBlock = kMrhsBlock / kMrhsGroup;
-
-template <typename R, int FMT>
-__device__ __forceinline__ Mat3<R> load_fat_m(const R *base, size_t vh, int p, int mu, int i) {
-    if constexpr (FMT == 1)
-        return load_link_r12(base, vh, p, mu, i);
-    else if constexpr (FMT == 2)
-        return load_link_r12h(base, vh, p, mu, i);
-    else
-        return load_link(base, vh, p, mu, i);
-}
 
 template <typename R>
 struct MParams {
@@ -49,23 +40,6 @@ struct MParams {
     double *partials;
     unsigned int *counter;
 };
-
-template <typename R, int EPI>
-__device__ __forceinline__ Vec3<R> mrhs_in(const MParams<R> &P, const R *pold, R beta, size_t off, size_t vh,
-                                           int j) {
-    if constexpr (EPI == EPI_PUPD) {
-        const Vec3<R> rv = load_vec(P.r + off, vh, j), pv = load_vec(pold + off, vh, j);
-        Vec3<R> v;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            v.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
-            v.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
-        }
-        return v;
-    } else {
-        return load_vec(P.in + off, vh, j);
-    }
-}
 
 template <typename R, int FMT, bool NAIK, int EPI>
 __global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParams<R> P) {
@@ -99,41 +73,19 @@ __global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParam
         const R beta = (EPI == EPI_PUPD) ? (R)S->beta[rh] : R(0);
         const size_t off = (size_t)rh * fstride;
         const Site s = site_of(g, p, i);
-        Vec3<R> acc;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = R(0);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const R eta = eta_bit(s, mu) ? R(-1) : R(1);
-            {
-                const int j = hop_index(g, s, mu, 1);
-                const Mat3<R> u = load_fat_m<R, FMT>(P.fat, vh, p, mu, i);
-                acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
-            }
-            {
-                const int j = hop_index(g, s, mu, -1);
-                const Mat3<R> u = load_fat_m<R, FMT>(P.fat, vh, 1 - p, mu, j);
-                acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
-            }
-            if (NAIK) {
-                const R e3 = P.c3 * eta;
-                {
-                    const int j = hop_index(g, s, mu, 3);
-                    const Mat3<R> u = load_link(P.lng, vh, p, mu, i);
-                    acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
-                }
-                {
-                    const int j = hop_index(g, s, mu, -3);
-                    const Mat3<R> u = load_link(P.lng, vh, 1 - p, mu, j);
-                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, mrhs_in<R, EPI>(P, pold, beta, off, vh, j));
-                }
-            }
-        }
+        const R *rin = (EPI == EPI_PUPD) ? P.r + off : P.in + off;
+        const R *pin = (EPI == EPI_PUPD) ? pold + off : nullptr;
+        const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, P.fat, P.lng, P.c3, p, i, s, [&](int j) {
+            if constexpr (EPI == EPI_PUPD)
+                return axpy_vec(rin, pin, beta, vh, j);
+            else
+                return load_vec(rin, vh, j);
+        });
         if constexpr (EPI == EPI_PLAIN) {
             store_vec(P.out + off, vh, i, acc);
         } else if constexpr (EPI == EPI_PUPD) {
             store_vec(P.out + off, vh, i, acc);
-            store_vec(pnew + off, vh, i, mrhs_in<R, EPI>(P, pold, beta, off, vh, i));
+            store_vec(pnew + off, vh, i, axpy_vec(rin, pin, beta, vh, i));
         } else if constexpr (EPI == EPI_NORMAL) {
             const Vec3<R> qv = load_vec(pnew + off, vh, i);
             Vec3<R> o;

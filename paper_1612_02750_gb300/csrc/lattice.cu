@@ -189,7 +189,7 @@ qex_status qex_lattice_create(const int dims[4], int antiperiodic_t, qex_lattice
 qex_status qex_lattice_destroy(qex_lattice *lat) {
     if (!lat) return QEX_OK;
     qex_status st = QEX_OK;
-    if (lat->partials || lat->work || lat->host_work) {
+    if (lat->partials || lat->work || lat->host_work || lat->batch_ctx) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize in destroy");
     }
@@ -202,6 +202,7 @@ qex_status qex_lattice_destroy(qex_lattice *lat) {
     if (lat->work) cudaFree(lat->work);
     if (lat->host_work) cudaFree(lat->host_work);
     if (lat->cg_graph) free_cg_graph(lat->cg_graph);
+    if (lat->batch_ctx) free_batch_ctx(lat->batch_ctx);
     if (lat->ev0) cudaEventDestroy(lat->ev0);
     if (lat->ev1) cudaEventDestroy(lat->ev1);
     delete lat;

@@ -366,6 +366,7 @@ struct qex_lattice {
     void *host_work;           // staging of qex_cg_host
     size_t host_work_bytes;
     void *cg_graph;            // cached CUDA graph of the last CG solve
+    void *batch_ctx;           // scratch of qex_cg_batch calls led by this lattice
     cudaEvent_t ev0, ev1;
 };
 

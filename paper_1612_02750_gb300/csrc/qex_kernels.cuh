@@ -132,5 +132,6 @@ int sm_count();
 void note_launches(unsigned long long n);
 void set_count_launches(bool on);
 void free_cg_graph(void *g);
+void free_batch_ctx(void *c);
 
 }  // namespace qex

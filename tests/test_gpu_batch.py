@@ -1,0 +1,116 @@
+"""Batched CG over independent lattices (qex_cg_batch) against the oracle and
+single-lattice solves."""
+
+import numpy as np
+import pytest
+
+import fieldgen as fg
+
+pytestmark = pytest.mark.gpu
+
+C3 = -1.0 / 24.0
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_02750_gb300 import build
+
+    build.build()
+    import paper_1612_02750_gb300 as mod
+
+    mod.load()
+    return mod
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _problem(q, dims, mass, seed, naik, inner, zero=False):
+    s = fg.rng_streams(seed)
+    u = fg.random_links(dims, "haar", s["links"])
+    w = fg.random_links(dims, "gauss3", s["long_links"]) if naik else None
+    b = fg.gaussian_field(s["source"], dims)
+    b[~fg.even_mask(dims)] = 0
+    if zero:
+        b[...] = 0
+    lat = q.Lattice(dims)
+    fat64 = q.qex_pack_links(lat, "f64", dev(u))
+    lng64 = q.qex_pack_links(lat, "f64", dev(w)) if naik else None
+    item = {"lat": lat, "fat64": fat64, "lng64": lng64, "mass": mass, "c_naik": C3 if naik else 0.0,
+            "b64": q.qex_pack_field(lat, "f64", 0, dev(b))}
+    if inner != "f64":
+        item["fat32"] = q.qex_convert_links(lat, "f64", fat64, inner)
+        item["lng32"] = q.qex_convert_links(lat, "f64", lng64, "f32") if naik else None
+    import torch
+
+    item["x64"] = torch.zeros_like(item["b64"])
+    return item, u, w, b
+
+
+SPECS = [((4, 4, 4, 4), 0.1), ((6, 4, 4, 10), 0.05), ((8, 8, 4, 8), 0.2), ((8, 4, 6, 8), 0.08), ((4, 6, 4, 4), 0.3)]
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32r12h"])
+@pytest.mark.parametrize("naik", [False, True])
+def test_batch_matches_oracle_and_single(q, oracle_mod, inner, naik):
+    """Five lattices of different extents and masses (one with a zero source)
+    solved in one batch: each meets an oracle-recomputed true residual of
+    1.05e-10 and agrees with its single-lattice solve."""
+    import torch
+
+    probs = [_problem(q, d, m, 70 + k, naik, inner, zero=(k == 3)) for k, (d, m) in enumerate(SPECS)]
+    st, stats = q.qex_cg_batch([p[0] for p in probs], inner, tol=1e-10, delta=0.1)
+    assert st == 0 and all(s["converged"] for s in stats), stats
+    for k, (item, u, w, b) in enumerate(probs):
+        dims = SPECS[k][0]
+        lat = item["lat"]
+        x = q.qex_unpack_field(lat, "f64", 0, item["x64"]).cpu().numpy()
+        if k == 3:
+            assert not x.any()
+            continue
+        tr = oracle_mod.true_residual(dims, u, b, x, item["mass"], w, item["c_naik"])
+        assert tr <= 1.05e-10, (k, tr)
+        x1 = torch.zeros_like(item["b64"])
+        q.qex_cg(lat, inner, item["fat64"], item["lng64"], item.get("fat32"), item.get("lng32"), item["c_naik"],
+                 item["mass"], item["b64"], x1, tol=1e-10, delta=0.1)
+        xs = q.qex_unpack_field(lat, "f64", 0, x1).cpu().numpy()
+        ev = fg.even_mask(dims)
+        assert relerr(x[ev], xs[ev]) <= 1e-7, k
+
+
+def test_batch_multi_lattice_workload_small(q, oracle_mod):
+    """The four smallest lattices of the multi-lattice workload (8^4, 12^4,
+    16^4, 16^3 x 32, Haar links, masses m_k = 0.005 * 20^(k/7)) in one batch
+    with 16-bit inner links: all converge to an oracle-checked 1e-10."""
+    dims_list = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32)]
+    masses = [0.005 * 20 ** (k / 7) for k in range(4)]
+    probs = [_problem(q, d, m, 4 + 10 * k, False, "f32r12h") for k, (d, m) in enumerate(zip(dims_list, masses))]
+    st, stats = q.qex_cg_batch([p[0] for p in probs], "f32r12h", tol=1e-10, maxiter=200000, delta=0.1)
+    assert st == 0 and all(s["converged"] for s in stats), stats
+    for k, (item, u, w, b) in enumerate(probs):
+        x = q.qex_unpack_field(item["lat"], "f64", 0, item["x64"]).cpu().numpy()
+        assert oracle_mod.true_residual(dims_list[k], u, b, x, masses[k]) <= 1.05e-10
+
+
+def test_batch_errors(q):
+    a, _, _, _ = _problem(q, (4, 4, 4, 4), 0.1, 80, False, "f64")
+    b, _, _, _ = _problem(q, (4, 4, 4, 4), 0.1, 81, True, "f64")
+    with pytest.raises(q.QexError) as e:
+        q.qex_cg_batch([a, b], "f64")  # Naik disagreement
+    assert e.value.status == 1
+    with pytest.raises(q.QexError) as e:
+        q.qex_cg_batch([a, dict(a)], "f64")  # shared lattice object
+    assert e.value.status == 1
+    with pytest.raises(q.QexError) as e:
+        q.qex_cg_batch([a], "f32r12h")  # no inner-precision links
+    assert e.value.status == 1
