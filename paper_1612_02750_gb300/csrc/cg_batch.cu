@@ -1,16 +1,22 @@
 // cg_batch.cu -- conjugate gradient on many independent lattices at once
-// (different extents, masses and links), each launch covering a work list of
+// (different extents, masses and links), every launch covering a work list of
 // (lattice, 256-site tile) items.
 //
 // Small lattices cannot fill the GPU on their own; batching them makes every
 // kernel of an iteration one launch over the tiles of all running lattices.
 // Each lattice keeps its own alpha, beta, norms and reliable-update state;
 // the lattices iterate in lockstep (the lockstep count's parity selects the
-// direction buffers), a lattice whose FP64 true residual meets tol stops
-// (its tiles return at once), and a reliable update requested by some
-// lattices is done for exactly those.  Reductions are per tile, summed per
-// lattice in tile order by the last block (bit-reproducible).
+// direction buffers).  The iteration kernels run a persistent grid over a
+// device-resident list of the running lattices' tiles, which the reliable
+// update recompacts whenever a lattice meets its FP64 true residual, so a
+// finished lattice costs nothing afterwards.  Reductions are per tile, summed
+// per lattice in tile order by the last block (bit-reproducible).  By
+// default the loop is one CUDA graph: a conditional WHILE node around the
+// three iteration kernels and a conditional IF node holding the reliable
+// update of the lattices that asked for one; QEX_CG_MODE=host drives the same
+// kernels from the host in batches.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -20,11 +26,12 @@
 
 namespace qex {
 
-constexpr int kTile = 256;  // sites per tile (one block)
+constexpr int kTile = 256;  // sites per tile
+constexpr int kBatchMinBlocks = 3;  // resident blocks per SM of the iteration kernels (no spills at 85 registers)
 
 struct LatDesc {
     Geom g;
-    int tile0, ntiles;
+    int tile0, ntiles;  // in the full tile list
     const void *fat_in, *lng_in;  // inner-precision links
     const double *fat64, *lng64;
     const double *b;
@@ -37,8 +44,11 @@ struct BatchScalars {
     double rr[kMaxRhs], pAp[kMaxRhs], alpha[kMaxRhs], beta[kMaxRhs], bb[kMaxRhs], stop2[kMaxRhs],
         rmax2[kMaxRhs], true_rr[kMaxRhs];
     int active[kMaxRhs], done[kMaxRhs], need[kMaxRhs], iters[kMaxRhs];
+    int alist[kMaxRhs];       // running lattices, in lattice order
+    int astart[kMaxRhs + 1];  // their first tile in the compacted list; astart[nlist] = tiles
+    int nlist;
     double tol2, delta2;
-    int n, iter, maxiter, halt, error, any_need, nactive, reliable_updates;
+    int n, iter, maxiter, halt, error, any_need, nactive, reliable_updates, trips;
 };
 
 enum BatchRole {
@@ -48,9 +58,22 @@ enum BatchRole {
     ROLE_RU2 = 3   // r64 = b - m^2 x64 + D_eo tmp64, ||r64||^2 -> flags (FP64, lattices in a reliable update)
 };
 
-__device__ __forceinline__ int lattice_of_tile(const LatDesc *d, int n, int t) {
+// Last index k with start[k] <= t (start sorted, start[0] = 0).
+__device__ __forceinline__ int find_start(const int *start, int n, int t) {
     int lo = 0, hi = n - 1;
-    while (lo < hi) {  // last lattice with tile0 <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int lattice_of_full_tile(const LatDesc *d, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (d[mid].tile0 <= t)
             lo = mid;
@@ -60,15 +83,34 @@ __device__ __forceinline__ int lattice_of_tile(const LatDesc *d, int n, int t) {
     return lo;
 }
 
-// Per-tile partial -> partials[t]; the last block sums each lattice's tiles
-// in order (one warp per lattice).  Returns true in the last block; the
-// per-lattice totals are then in tot[] (shared).
-__device__ __forceinline__ bool batch_reduce(double part, double *partials, unsigned int *counter, int n,
-                                             const LatDesc *d, double *smem, double *tot) {
+// Rebuild the running-lattice list from the active flags (one thread).
+__device__ __forceinline__ void compact_list(BatchScalars *S, const LatDesc *d, int n) {
+    int k = 0, t = 0;
+    for (int l = 0; l < n; ++l)
+        if (S->active[l]) {
+            S->alist[k] = l;
+            S->astart[k] = t;
+            t += d[l].ntiles;
+            ++k;
+        }
+    S->nlist = k;
+    S->astart[k] = t;
+}
+
+__device__ __forceinline__ void set_conds(const GraphCtl &ctl, unsigned int loop, unsigned int ru) {
+    if (ctl.active) {
+        cudaGraphSetConditional(ctl.loop, loop);
+        cudaGraphSetConditional(ctl.ru, ru);
+    }
+}
+
+// After the per-tile partials of this launch are written: the last block
+// sums each listed lattice's tiles in order (one warp per lattice) into tot[].
+__device__ __forceinline__ bool last_block_totals(double *partials, unsigned int *counter, int nl, const int *start,
+                                                  double *tot) {
     __shared__ unsigned int is_last;
-    const double bs = block_sum(part, smem);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = bs;
         __threadfence();
         const unsigned int t = atomicAdd(counter, 1u);
         is_last = (t == gridDim.x - 1) ? 1u : 0u;
@@ -77,71 +119,184 @@ __device__ __forceinline__ bool batch_reduce(double part, double *partials, unsi
     if (!is_last) return false;
     __threadfence();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int l = warp; l < n; l += nw) {
+    for (int k = warp; k < nl; k += nw) {
         double v = 0.0;
-        for (int k = lane; k < d[l].ntiles; k += 32) v += __ldcg(partials + d[l].tile0 + k);
+        for (int j = start[k] + lane; j < start[k + 1]; j += 32) v += __ldcg(partials + j);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) tot[l] = v;
+        if (lane == 0) tot[k] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) *counter = 0u;
     return true;
 }
 
+// Iteration Dslash kernels: persistent grid over the compacted tile list.
 template <typename R, int FMT, bool NAIK, int ROLE>
-__global__ void __launch_bounds__(kTile, 3)
-batch_dslash_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, double *partials,
-                    unsigned int *counter) {
+__global__ void __launch_bounds__(kTile, kBatchMinBlocks)
+batch_iter_dslash_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *partials, unsigned int *counter) {
     __shared__ double smem[32];
     __shared__ double tot[kMaxRhs];
-    if ((ROLE == ROLE_K1 || ROLE == ROLE_K2) && S->halt) return;  // uniform over the grid
-    const int l = lattice_of_tile(descs, n, blockIdx.x);
+    if (S->halt) return;  // uniform over the grid
+    const int nl = S->nlist;
+    const int ntiles = S->astart[nl];
+    const int it = S->iter;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int k = find_start(S->astart, nl, t);
+        const int l = S->alist[k];
+        const LatDesc &D = descs[l];
+        const Geom &g = D.g;
+        const size_t vh = (size_t)g.vh;
+        const int i = (t - S->astart[k]) * kTile + threadIdx.x;
+        const R *pold = (const R *)((it & 1) ? D.p1 : D.p0);
+        R *pnew = (R *)((it & 1) ? D.p0 : D.p1);
+        double part = 0.0;
+        if (i < g.vh) {
+            if constexpr (ROLE == ROLE_K1) {
+                const Site s = site_of(g, 1, i);
+                const R beta = (R)S->beta[l];
+                const R *r = (const R *)D.ri;
+                const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, (const R *)D.fat_in, (const R *)D.lng_in, (R)D.c3, 1,
+                                                              i, s, [&](int j) { return axpy_vec(r, pold, beta, vh, j); });
+                store_vec((R *)D.tmpi, vh, i, acc);
+                store_vec(pnew, vh, i, axpy_vec(r, pold, beta, vh, i));
+            } else {
+                const Site s = site_of(g, 0, i);
+                const R *tmp = (const R *)D.tmpi;
+                const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, (const R *)D.fat_in, (const R *)D.lng_in, (R)D.c3, 0,
+                                                              i, s, [&](int j) { return load_vec(tmp, vh, j); });
+                const Vec3<R> qv = load_vec((const R *)pnew, vh, i);
+                const R m2 = (R)D.m2;
+                Vec3<R> o;
+                R dd = R(0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    o.c[a].re = fma(m2, qv.c[a].re, -acc.c[a].re);
+                    o.c[a].im = fma(m2, qv.c[a].im, -acc.c[a].im);
+                    dd = fma(qv.c[a].re, o.c[a].re, dd);
+                    dd = fma(qv.c[a].im, o.c[a].im, dd);
+                }
+                store_vec((R *)D.api, vh, i, o);
+                part = (double)dd;
+            }
+        }
+        if constexpr (ROLE == ROLE_K2) {
+            const double bs = block_sum(part, smem);
+            if (threadIdx.x == 0) partials[t] = bs;
+        }
+    }
+    if constexpr (ROLE == ROLE_K2) {
+        if (!last_block_totals(partials, counter, nl, S->astart, tot)) return;
+        if (threadIdx.x != 0) return;
+        for (int k = 0; k < nl; ++k) {
+            const int l = S->alist[k];
+            const double v = tot[k];
+            S->pAp[l] = v;
+            if (!(v > 0.0) || !isfinite(v)) {
+                S->error = isfinite(v) ? 2 : 1;
+                S->halt = 1;
+            } else {
+                S->alpha[l] = S->rr[l] / v;
+            }
+        }
+    }
+}
+
+// x += alpha p_new; r -= alpha ap; ||r||^2 per lattice, then the decisions
+// and, in the graph solve, the loop and reliable-update conditions.
+template <typename R>
+__global__ void __launch_bounds__(kTile)
+batch_update_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *partials, unsigned int *counter,
+                    const GraphCtl ctl) {
+    __shared__ double smem[32];
+    __shared__ double tot[kMaxRhs];
+    if (S->halt) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_conds(ctl, 0u, 0u);
+        return;
+    }
+    // fail-safe: stop unless the last block sets the conditions again
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_conds(ctl, 0u, 0u);
+    const int nl = S->nlist;
+    const int ntiles = S->astart[nl];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int k = find_start(S->astart, nl, t);
+        const int l = S->alist[k];
+        const LatDesc &D = descs[l];
+        const size_t vh = (size_t)D.g.vh;
+        const int i = (t - S->astart[k]) * kTile + threadIdx.x;
+        double part = 0.0;
+        if (i < D.g.vh) {
+            const R alpha = (R)S->alpha[l];
+            const R *p = (const R *)((S->iter & 1) ? D.p0 : D.p1);
+            R *x = (R *)D.xi, *r = (R *)D.ri;
+            Vec3<R> xv = load_vec(x, vh, i), rv = load_vec(r, vh, i);
+            const Vec3<R> pv = load_vec(p, vh, i), av = load_vec((const R *)D.api, vh, i);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
+                xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
+                rv.c[a].re = fma(-alpha, av.c[a].re, rv.c[a].re);
+                rv.c[a].im = fma(-alpha, av.c[a].im, rv.c[a].im);
+                part += (double)(rv.c[a].re * rv.c[a].re + rv.c[a].im * rv.c[a].im);
+            }
+            store_vec(x, vh, i, xv);
+            store_vec(r, vh, i, rv);
+        }
+        const double bs = block_sum(part, smem);
+        if (threadIdx.x == 0) partials[t] = bs;
+    }
+    if (!last_block_totals(partials, counter, nl, S->astart, tot)) return;
+    if (threadIdx.x != 0) return;
+    S->iter += 1;
+    S->trips += 1;
+    int any = 0;
+    for (int k = 0; k < nl; ++k) {
+        const int l = S->alist[k];
+        const double v = tot[k];
+        S->iters[l] += 1;
+        if (!isfinite(v)) {
+            S->error = 1;
+            continue;
+        }
+        if (v > S->rmax2[l]) S->rmax2[l] = v;
+        if (v <= S->stop2[l] || v < S->delta2 * S->rmax2[l] || S->iter >= S->maxiter) {
+            S->need[l] = 1;  // rr keeps its old value: beta comes from the true residual
+            any = 1;
+        } else {
+            S->beta[l] = v / S->rr[l];
+            S->rr[l] = v;
+        }
+    }
+    S->any_need = any;
+    S->halt = (any || S->error) ? 1 : 0;
+    const unsigned int go = (!S->error && S->trips < S->maxiter + 4) ? 1u : 0u;
+    set_conds(ctl, go, (go && any) ? 1u : 0u);
+}
+
+// Reliable update, FP64 Dslash over the full tile list (lattices with need set).
+template <bool NAIK, int ROLE>
+__global__ void __launch_bounds__(kTile, 3)
+batch_ru_dslash_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, const int *need, double *partials,
+                       unsigned int *counter) {
+    __shared__ double smem[32];
+    __shared__ double tot[kMaxRhs];
+    __shared__ int ident[kMaxRhs + 1];
+    const int l = lattice_of_full_tile(descs, n, blockIdx.x);
     const LatDesc &D = descs[l];
-    const bool fp64 = ROLE == ROLE_RU1 || ROLE == ROLE_RU2;
-    const bool run = fp64 ? S->need[l] != 0 : S->active[l] != 0;  // uniform over the block
-    const int p = (ROLE == ROLE_K1 || ROLE == ROLE_RU1) ? 1 : 0;
     const Geom &g = D.g;
     const size_t vh = (size_t)g.vh;
     const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
-    const int it = S->iter;
-    const R *pold = (const R *)((it & 1) ? D.p1 : D.p0);
-    R *pnew = (R *)((it & 1) ? D.p0 : D.p1);
     double part = 0.0;
-    if (run && i < g.vh) {
-        const Site s = site_of(g, p, i);
-        if constexpr (ROLE == ROLE_K1) {
-            const R beta = (R)S->beta[l];
-            const R *r = (const R *)D.ri;
-            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, (const R *)D.fat_in, (const R *)D.lng_in, (R)D.c3, p, i,
-                                                          s, [&](int j) { return axpy_vec(r, pold, beta, vh, j); });
-            store_vec((R *)D.tmpi, vh, i, acc);
-            store_vec(pnew, vh, i, axpy_vec(r, pold, beta, vh, i));
-        } else if constexpr (ROLE == ROLE_K2) {
-            const R *tmp = (const R *)D.tmpi;
-            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, (const R *)D.fat_in, (const R *)D.lng_in, (R)D.c3, p, i,
-                                                          s, [&](int j) { return load_vec(tmp, vh, j); });
-            const Vec3<R> qv = load_vec((const R *)pnew, vh, i);
-            const R m2 = (R)D.m2;
-            Vec3<R> o;
-            R dd = R(0);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                o.c[a].re = fma(m2, qv.c[a].re, -acc.c[a].re);
-                o.c[a].im = fma(m2, qv.c[a].im, -acc.c[a].im);
-                dd = fma(qv.c[a].re, o.c[a].re, dd);
-                dd = fma(qv.c[a].im, o.c[a].im, dd);
-            }
-            store_vec((R *)D.api, vh, i, o);
-            part = (double)dd;
-        } else if constexpr (ROLE == ROLE_RU1) {
+    if (need[l] && i < g.vh) {
+        if constexpr (ROLE == ROLE_RU1) {
+            const Site s = site_of(g, 1, i);
             const double *x = D.x64;
-            const Vec3<double> acc = dslash_site<double, 0, NAIK>(g, D.fat64, D.lng64, D.c3, p, i, s,
-                                                                  [&](int j) { return load_vec(x, vh, j); });
-            store_vec(D.tmp64, vh, i, acc);
+            store_vec(D.tmp64, vh, i, dslash_site<double, 0, NAIK>(g, D.fat64, D.lng64, D.c3, 1, i, s,
+                                                                   [&](int j) { return load_vec(x, vh, j); }));
         } else {
+            const Site s = site_of(g, 0, i);
             const double *tmp = D.tmp64;
-            const Vec3<double> acc = dslash_site<double, 0, NAIK>(g, D.fat64, D.lng64, D.c3, p, i, s,
+            const Vec3<double> acc = dslash_site<double, 0, NAIK>(g, D.fat64, D.lng64, D.c3, 0, i, s,
                                                                   [&](int j) { return load_vec(tmp, vh, j); });
             const Vec3<double> xv = load_vec(D.x64, vh, i), bv = load_vec(D.b, vh, i);
             Vec3<double> o;
@@ -155,117 +310,50 @@ batch_dslash_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, d
             store_vec(D.r64, vh, i, o);
         }
     }
-    if constexpr (ROLE == ROLE_K1 || ROLE == ROLE_RU1) {
-        return;
-    } else {
-        if (!batch_reduce(part, partials, counter, n, descs, smem, tot)) return;
+    if constexpr (ROLE == ROLE_RU2) {
+        const double bs = block_sum(part, smem);
+        if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+        if (threadIdx.x == 0)  // per-lattice tile ranges of the full list
+            for (int k = 0; k <= n; ++k) ident[k] = k < n ? descs[k].tile0 : descs[n - 1].tile0 + descs[n - 1].ntiles;
+        if (!last_block_totals(partials, counter, n, ident, tot)) return;
         if (threadIdx.x != 0) return;
         for (int k = 0; k < n; ++k) {
+            if (!need[k] || !S->need[k]) continue;
             const double v = tot[k];
-            if constexpr (ROLE == ROLE_K2) {
-                if (!S->active[k]) continue;
-                S->pAp[k] = v;
-                if (!(v > 0.0) || !isfinite(v)) {
-                    S->error = isfinite(v) ? 2 : 1;
-                    S->halt = 1;
-                } else {
-                    S->alpha[k] = S->rr[k] / v;
-                }
-            } else {
-                if (!S->need[k]) continue;
-                S->need[k] = 0;
-                S->true_rr[k] = v;
-                if (!isfinite(v)) {
-                    S->error = 1;
-                    continue;
-                }
-                S->beta[k] = S->rr[k] > 0.0 ? v / S->rr[k] : 0.0;
-                S->rr[k] = v;
-                S->rmax2[k] = v;
-                if (v <= S->stop2[k]) {
-                    S->done[k] = 1;
-                    S->active[k] = 0;
-                }
+            S->need[k] = 0;
+            S->true_rr[k] = v;
+            if (!isfinite(v)) {
+                S->error = 1;
+                continue;
+            }
+            S->beta[k] = S->rr[k] > 0.0 ? v / S->rr[k] : 0.0;
+            S->rr[k] = v;
+            S->rmax2[k] = v;
+            if (v <= S->stop2[k]) {
+                S->done[k] = 1;
+                S->active[k] = 0;
             }
         }
-        if constexpr (ROLE == ROLE_RU2) {
-            int na = 0;
-            for (int k = 0; k < n; ++k) na += S->active[k];
-            S->nactive = na;
-            S->any_need = 0;
-            S->reliable_updates += 1;
-            S->halt = (na == 0 || S->iter >= S->maxiter || S->error) ? 1 : 0;
-        }
+        compact_list(S, descs, n);
+        S->nactive = S->nlist;
+        S->any_need = 0;
+        S->reliable_updates += 1;
+        S->halt = (S->nlist == 0 || S->iter >= S->maxiter || S->error) ? 1 : 0;
     }
 }
 
-// x += alpha p_new; r -= alpha ap; ||r||^2 per lattice, then the decisions.
-template <typename R>
-__global__ void __launch_bounds__(kTile)
-batch_update_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, double *partials,
-                    unsigned int *counter) {
-    __shared__ double smem[32];
-    __shared__ double tot[kMaxRhs];
-    if (S->halt) return;
-    const int l = lattice_of_tile(descs, n, blockIdx.x);
-    const LatDesc &D = descs[l];
-    const size_t vh = (size_t)D.g.vh;
-    const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
-    double part = 0.0;
-    if (S->active[l] && i < D.g.vh) {
-        const R alpha = (R)S->alpha[l];
-        const R *p = (const R *)((S->iter & 1) ? D.p0 : D.p1);
-        R *x = (R *)D.xi, *r = (R *)D.ri;
-        Vec3<R> xv = load_vec(x, vh, i), rv = load_vec(r, vh, i);
-        const Vec3<R> pv = load_vec(p, vh, i), av = load_vec((const R *)D.api, vh, i);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
-            xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
-            rv.c[a].re = fma(-alpha, av.c[a].re, rv.c[a].re);
-            rv.c[a].im = fma(-alpha, av.c[a].im, rv.c[a].im);
-            part += (double)(rv.c[a].re * rv.c[a].re + rv.c[a].im * rv.c[a].im);
-        }
-        store_vec(x, vh, i, xv);
-        store_vec(r, vh, i, rv);
-    }
-    if (!batch_reduce(part, partials, counter, n, descs, smem, tot)) return;
-    if (threadIdx.x != 0) return;
-    S->iter += 1;
-    int any = 0;
-    for (int k = 0; k < n; ++k) {
-        if (!S->active[k]) continue;
-        const double v = tot[k];
-        S->iters[k] += 1;
-        if (!isfinite(v)) {
-            S->error = 1;
-            continue;
-        }
-        if (v > S->rmax2[k]) S->rmax2[k] = v;
-        if (v <= S->stop2[k] || v < S->delta2 * S->rmax2[k] || S->iter >= S->maxiter) {
-            S->need[k] = 1;  // rr keeps its old value: beta comes from the true residual
-            any = 1;
-        } else {
-            S->beta[k] = v / S->rr[k];
-            S->rr[k] = v;
-        }
-    }
-    S->any_need = any;
-    S->halt = (any || S->error) ? 1 : 0;
-}
-
-// Reliable-update helpers over the lattices with need set (mixed precision):
+// Reliable-update vector steps over the full tile list (lattices in `need`):
 // x64 += xh, xh = 0 before the FP64 residual; r_inner = (float) r64 after it.
-template <bool ACCUM>
+template <int STEP>
 __global__ void __launch_bounds__(kTile)
-batch_ru_vectors_kernel(const LatDesc *__restrict__ descs, int n, const BatchScalars *S, const int *need_snapshot) {
-    const int l = lattice_of_tile(descs, n, blockIdx.x);
-    if (!need_snapshot[l]) return;
+batch_ru_vectors_kernel(const LatDesc *__restrict__ descs, int n, const int *need) {
+    const int l = lattice_of_full_tile(descs, n, blockIdx.x);
+    if (!need[l]) return;
     const LatDesc &D = descs[l];
     const size_t vh = (size_t)D.g.vh;
     const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
     if (i >= D.g.vh) return;
-    if (ACCUM) {
+    if (STEP == 0) {
         Vec3<double> xv = load_vec(D.x64, vh, i);
         const Vec3<float> hv = load_vec((const float *)D.xi, vh, i);
         Vec3<float> z;
@@ -289,13 +377,25 @@ batch_ru_vectors_kernel(const LatDesc *__restrict__ descs, int n, const BatchSca
     }
 }
 
+// End of a reliable update in the graph solve: the loop condition.
+__global__ void batch_setcond_kernel(const BatchScalars *S, const GraphCtl ctl) {
+    if (ctl.active && threadIdx.x == 0)
+        cudaGraphSetConditional(ctl.loop, (!S->halt && S->trips < S->maxiter + 4) ? 1u : 0u);
+}
+
+// Snapshot of need[] for the update's vector steps (the residual clears it).
+__global__ void batch_snap_kernel(const BatchScalars *S, int *need, int n) {
+    if (threadIdx.x < n) need[threadIdx.x] = S->need[threadIdx.x];
+}
+
 // ||b||^2 per lattice (stop criterion); zero sources are solved (x = 0).
 __global__ void __launch_bounds__(kTile)
 batch_norm2_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, double *partials,
                    unsigned int *counter) {
     __shared__ double smem[32];
     __shared__ double tot[kMaxRhs];
-    const int l = lattice_of_tile(descs, n, blockIdx.x);
+    __shared__ int ident[kMaxRhs + 1];
+    const int l = lattice_of_full_tile(descs, n, blockIdx.x);
     const LatDesc &D = descs[l];
     const size_t vh = (size_t)D.g.vh;
     const int i = (blockIdx.x - D.tile0) * kTile + threadIdx.x;
@@ -305,7 +405,12 @@ batch_norm2_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, do
 #pragma unroll
         for (int a = 0; a < 3; ++a) part += v.c[a].re * v.c[a].re + v.c[a].im * v.c[a].im;
     }
-    if (!batch_reduce(part, partials, counter, n, descs, smem, tot)) return;
+    const double bs = block_sum(part, smem);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = bs;
+        for (int k = 0; k <= n; ++k) ident[k] = k < n ? descs[k].tile0 : descs[n - 1].tile0 + descs[n - 1].ntiles;
+    }
+    if (!last_block_totals(partials, counter, n, ident, tot)) return;
     if (threadIdx.x != 0) return;
     for (int k = 0; k < n; ++k) {
         S->bb[k] = tot[k];
@@ -320,7 +425,7 @@ batch_norm2_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, do
     }
 }
 
-// Batch scratch, owned by the first item's lattice.
+// Batch scratch and cached graph, owned by the first item's lattice.
 struct BatchCtx {
     LatDesc *descs;
     BatchScalars *S;
@@ -328,12 +433,19 @@ struct BatchCtx {
     int *need_snap;
     double *partials;
     unsigned int *counter;
-    int cap_lat, cap_tiles;
+    int cap_tiles;
+    // graph cache key and graph
+    int g_n, g_tiles, g_naik;
+    qex_prec g_inner;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
 };
 
 void free_batch_ctx(void *p) {
     BatchCtx *c = (BatchCtx *)p;
     if (!c) return;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     cudaFree(c->descs);
     cudaFree(c->S);
     cudaFreeHost(c->host);
@@ -348,36 +460,153 @@ static size_t al256b(size_t n) { return (n + 255) & ~size_t(255); }
 qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                              const void *in, const void *out);
 
+struct BatchLaunch {
+    const BatchCtx *c;
+    int n, total_tiles, iter_grid;
+    qex_prec inner;
+    bool naik, mixed;
+};
+
 template <typename R, int FMT, bool NAIK>
-static void launch_role(int role, int ntiles, const BatchCtx *c, int n, cudaStream_t s) {
+static void launch_iter_t(const BatchLaunch &b, int role, cudaStream_t s) {
     if (role == ROLE_K1)
-        batch_dslash_kernel<R, FMT, NAIK, ROLE_K1><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
-    else if (role == ROLE_K2)
-        batch_dslash_kernel<R, FMT, NAIK, ROLE_K2><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
-    else if (role == ROLE_RU1)
-        batch_dslash_kernel<R, FMT, NAIK, ROLE_RU1><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+        batch_iter_dslash_kernel<R, FMT, NAIK, ROLE_K1><<<b.iter_grid, kTile, 0, s>>>(b.c->descs, b.c->S,
+                                                                                       b.c->partials, b.c->counter);
     else
-        batch_dslash_kernel<R, FMT, NAIK, ROLE_RU2><<<ntiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
+        batch_iter_dslash_kernel<R, FMT, NAIK, ROLE_K2><<<b.iter_grid, kTile, 0, s>>>(b.c->descs, b.c->S,
+                                                                                       b.c->partials, b.c->counter);
 }
 
 template <typename R, int FMT>
-static void launch_role_naik(bool naik, int role, int ntiles, const BatchCtx *c, int n, cudaStream_t s) {
-    if (naik)
-        launch_role<R, FMT, true>(role, ntiles, c, n, s);
+static void launch_iter_n(const BatchLaunch &b, int role, cudaStream_t s) {
+    if (b.naik)
+        launch_iter_t<R, FMT, true>(b, role, s);
     else
-        launch_role<R, FMT, false>(role, ntiles, c, n, s);
+        launch_iter_t<R, FMT, false>(b, role, s);
 }
 
-static void launch_batch_dslash(qex_prec inner, bool naik, int role, int ntiles, const BatchCtx *c, int n,
-                                cudaStream_t s) {
-    if (inner == QEX_F64)
-        launch_role_naik<double, 0>(naik, role, ntiles, c, n, s);
-    else if (inner == QEX_F32_R12)
-        launch_role_naik<float, 1>(naik, role, ntiles, c, n, s);
-    else if (inner == QEX_F32_R12H)
-        launch_role_naik<float, 2>(naik, role, ntiles, c, n, s);
+static qex_status enqueue_iteration(const BatchLaunch &b, const GraphCtl &ctl, cudaStream_t s) {
+    for (int role = ROLE_K1; role <= ROLE_K2; ++role) {
+        if (b.inner == QEX_F64)
+            launch_iter_n<double, 0>(b, role, s);
+        else if (b.inner == QEX_F32_R12)
+            launch_iter_n<float, 1>(b, role, s);
+        else if (b.inner == QEX_F32_R12H)
+            launch_iter_n<float, 2>(b, role, s);
+        else
+            launch_iter_n<float, 0>(b, role, s);
+        QEX_CHECK_LAUNCH("batch_iter_dslash_kernel");
+    }
+    if (b.mixed)
+        batch_update_kernel<float><<<b.iter_grid, kTile, 0, s>>>(b.c->descs, b.c->S, b.c->partials, b.c->counter, ctl);
     else
-        launch_role_naik<float, 0>(naik, role, ntiles, c, n, s);
+        batch_update_kernel<double><<<b.iter_grid, kTile, 0, s>>>(b.c->descs, b.c->S, b.c->partials, b.c->counter,
+                                                                  ctl);
+    QEX_CHECK_LAUNCH("batch_update_kernel");
+    return QEX_OK;
+}
+
+static qex_status enqueue_reliable_update(const BatchLaunch &b, const GraphCtl &ctl, cudaStream_t s) {
+    const BatchCtx *c = b.c;
+    batch_snap_kernel<<<1, kMaxRhs, 0, s>>>(c->S, c->need_snap, b.n);
+    QEX_CHECK_LAUNCH("batch_snap_kernel");
+    if (b.mixed) {
+        batch_ru_vectors_kernel<0><<<b.total_tiles, kTile, 0, s>>>(c->descs, b.n, c->need_snap);
+        QEX_CHECK_LAUNCH("batch_ru_vectors_kernel");
+    }
+    if (b.naik) {
+        batch_ru_dslash_kernel<true, ROLE_RU1><<<b.total_tiles, kTile, 0, s>>>(c->descs, b.n, c->S, c->need_snap,
+                                                                             c->partials, c->counter);
+        QEX_CHECK_LAUNCH("batch_ru_dslash_kernel");
+        batch_ru_dslash_kernel<true, ROLE_RU2><<<b.total_tiles, kTile, 0, s>>>(c->descs, b.n, c->S, c->need_snap,
+                                                                             c->partials, c->counter);
+    } else {
+        batch_ru_dslash_kernel<false, ROLE_RU1><<<b.total_tiles, kTile, 0, s>>>(c->descs, b.n, c->S, c->need_snap,
+                                                                              c->partials, c->counter);
+        QEX_CHECK_LAUNCH("batch_ru_dslash_kernel");
+        batch_ru_dslash_kernel<false, ROLE_RU2><<<b.total_tiles, kTile, 0, s>>>(c->descs, b.n, c->S, c->need_snap,
+                                                                              c->partials, c->counter);
+    }
+    QEX_CHECK_LAUNCH("batch_ru_dslash_kernel");
+    if (b.mixed) {
+        batch_ru_vectors_kernel<1><<<b.total_tiles, kTile, 0, s>>>(c->descs, b.n, c->need_snap);
+        QEX_CHECK_LAUNCH("batch_ru_vectors_kernel");
+    }
+    if (ctl.active) {
+        batch_setcond_kernel<<<1, 32, 0, s>>>(c->S, ctl);
+        QEX_CHECK_LAUNCH("batch_setcond_kernel");
+    }
+    return QEX_OK;
+}
+
+static qex_status build_batch_graph(BatchCtx *c, const BatchLaunch &b) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaSuccess;
+    qex_status st = QEX_OK;
+    set_count_launches(false);
+    do {
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) break;
+        if ((e = cudaGraphCreate(&c->graph, 0))) break;
+        GraphCtl ctl = {};
+        ctl.active = 1;
+        if ((e = cudaGraphConditionalHandleCreate(&ctl.loop, c->graph, 1, cudaGraphCondAssignDefault))) break;
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = ctl.loop;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        if ((e = cudaGraphAddNode(&wnode, c->graph, nullptr, nullptr, 0, &wp))) break;
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        if ((e = cudaGraphConditionalHandleCreate(&ctl.ru, body, 0, 0))) break;
+        if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
+        st = enqueue_iteration(b, ctl, cs);
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t capg = nullptr;
+        cudaGraphNodeParams ip = {};
+        cudaGraphNode_t inode = nullptr;
+        if (!st) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps);
+        if (!st && !e) {
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = ctl.ru;
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            e = cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip);
+        }
+        if (!st && !e) e = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+        if (st) break;
+        if (e || (e = e2)) break;
+        if ((e = cudaStreamBeginCaptureToGraph(cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeRelaxed)))
+            break;
+        st = enqueue_reliable_update(b, ctl, cs);
+        e2 = cudaStreamEndCapture(cs, &captured);
+        if (st) break;
+        if ((e = e2)) break;
+        if ((e = cudaGraphInstantiate(&c->exec, c->graph, 0))) break;
+    } while (0);
+    set_count_launches(true);
+    if (cs) cudaStreamDestroy(cs);
+    if (st || e) {
+        if (c->exec) cudaGraphExecDestroy(c->exec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->exec = nullptr;
+        c->graph = nullptr;
+        return st ? st : cuda_fail(e, "building the batched CG graph");
+    }
+    c->g_n = b.n;
+    c->g_tiles = b.total_tiles;
+    c->g_naik = b.naik;
+    c->g_inner = b.inner;
+    return QEX_OK;
 }
 
 }  // namespace qex
@@ -419,6 +648,8 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
     }
     const cudaStream_t s = as_stream(stream);
     qex_lattice *own = const_cast<qex_lattice *>(items[0].lat);
+    const char *mode = getenv("QEX_CG_MODE");
+    const bool use_graph = !(mode && strcmp(mode, "host") == 0);
 
     // per-lattice work vectors in each lattice's own work area
     std::vector<LatDesc> descs(n);
@@ -468,7 +699,7 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
 
     // batch scratch on the first lattice
     BatchCtx *c = (BatchCtx *)own->batch_ctx;
-    if (!c || c->cap_lat < n || c->cap_tiles < total_tiles) {
+    if (!c || c->cap_tiles < total_tiles) {
         if (c) {
             QEX_CUDA(cudaStreamSynchronize(s));
             free_batch_ctx(c);
@@ -476,8 +707,8 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
         }
         c = new BatchCtx;
         memset(c, 0, sizeof(*c));
-        c->cap_lat = QEX_BATCH_MAX;
         c->cap_tiles = total_tiles;
+        own->batch_ctx = c;
         QEX_CUDA(cudaMalloc(&c->descs, sizeof(LatDesc) * QEX_BATCH_MAX));
         QEX_CUDA(cudaMalloc(&c->S, sizeof(BatchScalars)));
         QEX_CUDA(cudaMallocHost(&c->host, sizeof(BatchScalars)));
@@ -485,8 +716,22 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
         QEX_CUDA(cudaMalloc(&c->partials, sizeof(double) * total_tiles));
         QEX_CUDA(cudaMalloc(&c->counter, sizeof(unsigned int)));
         QEX_CUDA(cudaMemset(c->counter, 0, sizeof(unsigned int)));
-        own->batch_ctx = c;
     }
+    BatchLaunch b;
+    b.c = c;
+    b.n = n;
+    b.total_tiles = total_tiles;
+    const int resident = sm_count() * kBatchMinBlocks;
+    b.iter_grid = total_tiles < resident ? total_tiles : resident;
+    b.inner = inner;
+    b.naik = naik;
+    b.mixed = mixed;
+    if (use_graph && !(c->exec && c->g_n == n && c->g_tiles == total_tiles && c->g_naik == (int)naik &&
+                       c->g_inner == inner)) {
+        QEX_CUDA(cudaStreamSynchronize(s));
+        if ((st = build_batch_graph(c, b))) return st;
+    }
+
     QEX_CUDA(cudaStreamSynchronize(s));  // the pinned slot is free
     BatchScalars *h = c->host;
     memset(h, 0, sizeof(*h));
@@ -509,53 +754,34 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
     }
     batch_norm2_kernel<<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
     QEX_CHECK_LAUNCH("batch_norm2_kernel");
-
-    auto reliable_update = [&]() -> qex_status {
-        // lattices in the update: snapshot of need (the residual kernel clears it)
-        QEX_CUDA(cudaMemcpyAsync(c->need_snap, c->S->need, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
-        if (mixed) {
-            batch_ru_vectors_kernel<true><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->need_snap);
-            QEX_CHECK_LAUNCH("batch_ru_vectors_kernel");
-        }
-        launch_batch_dslash(QEX_F64, naik, ROLE_RU1, total_tiles, c, n, s);
-        QEX_CHECK_LAUNCH("batch_dslash_kernel");
-        launch_batch_dslash(QEX_F64, naik, ROLE_RU2, total_tiles, c, n, s);
-        QEX_CHECK_LAUNCH("batch_dslash_kernel");
-        if (mixed) {
-            batch_ru_vectors_kernel<false><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->need_snap);
-            QEX_CHECK_LAUNCH("batch_ru_vectors_kernel");
-        }
-        return QEX_OK;
-    };
-    auto iteration = [&]() -> qex_status {
-        launch_batch_dslash(inner, naik, ROLE_K1, total_tiles, c, n, s);
-        QEX_CHECK_LAUNCH("batch_dslash_kernel");
-        launch_batch_dslash(inner, naik, ROLE_K2, total_tiles, c, n, s);
-        QEX_CHECK_LAUNCH("batch_dslash_kernel");
-        if (mixed)
-            batch_update_kernel<float><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
-        else
-            batch_update_kernel<double><<<total_tiles, kTile, 0, s>>>(c->descs, n, c->S, c->partials, c->counter);
-        QEX_CHECK_LAUNCH("batch_update_kernel");
-        return QEX_OK;
-    };
+    const GraphCtl off = {};
     auto fetch = [&]() -> qex_status {
         QEX_CUDA(cudaMemcpyAsync(h, c->S, sizeof(BatchScalars), cudaMemcpyDeviceToHost, s));
         QEX_CUDA(cudaStreamSynchronize(s));
         return QEX_OK;
     };
-
-    if ((st = reliable_update()) || (st = fetch())) return st;
+    // the first FP64 residual of every lattice, outside the loop (it also
+    // builds the running-lattice list)
+    if ((st = enqueue_reliable_update(b, off, s)) || (st = fetch())) return st;
     for (int k = 0; k < n; ++k)  // zero sources: x = 0 exactly
         if (h->bb[k] == 0.0) QEX_CUDA(cudaMemsetAsync(items[k].x64, 0, (size_t)items[k].lat->vh * 48, s));
-    const int batch = 8;
-    while (!st && !h->error && !h->halt) {
-        for (int k = 0; k < batch && !st; ++k) st = iteration();
-        if (st || (st = fetch())) break;
-        if (h->error || !h->any_need) continue;
-        if ((st = reliable_update()) || (st = fetch())) break;
+    if (!h->error && !h->halt) {
+        if (use_graph) {
+            QEX_CUDA(cudaGraphLaunch(c->exec, s));
+            if ((st = fetch())) return st;
+            note_launches(3ull * (unsigned long long)h->trips +
+                          (mixed ? 6ull : 4ull) * (unsigned long long)(h->reliable_updates > 1 ? h->reliable_updates - 1 : 0));
+        } else {
+            const int batch = 8;
+            while (!st && !h->error && !h->halt) {
+                for (int k = 0; k < batch && !st; ++k) st = enqueue_iteration(b, off, s);
+                if (st || (st = fetch())) break;
+                if (h->error || !h->any_need) continue;
+                if ((st = enqueue_reliable_update(b, off, s)) || (st = fetch())) break;
+            }
+            if (st) return st;
+        }
     }
-    if (st) return st;
     QEX_CUDA(cudaEventRecord(t1, s));
     QEX_CUDA(cudaEventSynchronize(t1));
     float ms = 0.f;

@@ -114,3 +114,31 @@ def test_batch_errors(q):
     with pytest.raises(q.QexError) as e:
         q.qex_cg_batch([a], "f32r12h")  # no inner-precision links
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32r12h"])
+def test_batch_graph_matches_host_loop(q, monkeypatch, inner):
+    """The CUDA-graph batch loop and the host-driven loop run the same kernels
+    in the same order: identical iteration counts and bitwise-equal solutions."""
+    import torch
+
+    runs = []
+    for mode in ("graph", "host"):
+        if mode == "host":
+            monkeypatch.setenv("QEX_CG_MODE", "host")
+        probs = [_problem(q, d, m, 90 + k, True, inner) for k, (d, m) in enumerate(SPECS)]
+        st, stats = q.qex_cg_batch([p[0] for p in probs], inner, tol=1e-10, delta=0.1)
+        assert st == 0
+        runs.append(([s["iters"] for s in stats], [p[0]["x64"].clone() for p in probs]))
+    assert runs[0][0] == runs[1][0]
+    for a, b in zip(runs[0][1], runs[1][1]):
+        assert torch.equal(a, b)
+
+
+def test_batch_maxiter_stops_every_lattice(q):
+    """A cap below what the lattices need: the solve stops at the cap with
+    QEX_ERR_NOT_CONVERGED (status 5) and reports each lattice's count."""
+    probs = [_problem(q, d, m, 100 + k, False, "f32r12h") for k, (d, m) in enumerate(SPECS[:3])]
+    st, stats = q.qex_cg_batch([p[0] for p in probs], "f32r12h", tol=1e-12, maxiter=7, delta=0.1, check=False)
+    assert st == 5
+    assert [s["iters"] for s in stats] == [7, 7, 7] and not any(s["converged"] for s in stats)
