@@ -34,8 +34,9 @@
  *            element c = 3a+b); F32: 4 planes of float4 (elements 0-1, 2-3,
  *            4-5, 6-7) and 1 plane of float2 (element 8); F32_R12: 3 planes
  *            of float4 (elements 0-1, 2-3, 4-5: rows 0 and 1); F32_R12H: 1
- *            plane of 8 int16 (elements 0-3) and 1 plane of 4 int16
- *            (elements 4-5), re before im.  Size qex_links_bytes().
+ *            plane of 16-byte words (elements 0-3) and 1 plane of 8-byte
+ *            words (elements 4-5), one 32-bit word per element: re in the
+ *            low, im in the high 16 bits.  Size qex_links_bytes().
  *     half field (the Vh sites of one parity): F64: 3 planes of double2
  *            (colour a); F32, F32_R12 and F32_R12H: 1 plane of float4
  *            (colours 0,1) + 1 plane of float2 (colour 2).  Size
@@ -78,8 +79,9 @@ typedef enum {
  * kernel as the complex conjugate of the cross product of the first two,
  * which is exact for SU(3) matrices only -- use it for unitary, unimodular
  * links.  QEX_F32_R12H is the same with each of the 12 reals stored as a
- * 16-bit fixed-point number (int16 q, value q / 32767; SU(3) entries lie in
- * [-1, 1]), quantisation error <= 1.5e-5 per real: an inner-solver format
+ * 16-bit fixed-point number (q = round(32767 v) in [-32767, 32767], stored
+ * as the unsigned offset-binary q + 32768; value q / 32767; SU(3) entries
+ * lie in [-1, 1]), quantisation error <= 1.5e-5 per real: an inner-solver format
  * (use it inside mixed-precision CG, whose FP64 reliable updates correct
  * it).  Long (Naik) links are never compressed: with QEX_F32_R12 or
  * QEX_F32_R12H the long link set is in QEX_F32 format. */

@@ -1,7 +1,7 @@
 // blas.cu -- fused CG vector updates and deterministic FP64 reductions.
 //
 // Grid-stride kernels over the Vh sites of one parity with a fixed grid per
-// lattice (at most 8 blocks per SM), so the per-block partial sums -- and
+// lattice (at most QEX_BLAS_BLOCKS_PER_SM blocks per SM), so the per-block partial sums -- and
 // therefore every reduction -- come out bit-identical run to run.  Sums are
 // formed per site in the vector precision and accumulated across sites in
 // FP64.
@@ -168,6 +168,15 @@ finish_ru_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32
         cudaGraphSetConditional(ctl.loop, (!S->halt && S->trips < S->maxiter + 4) ? 1u : 0u);
 }
 
+__global__ void __launch_bounds__(kBlock) any_nonzero_kernel(size_t n2, const double2 *__restrict__ f, int *flag) {
+    int nz = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = __ldg(f + i);
+        nz |= (v.x != 0.0 || v.y != 0.0) ? 1 : 0;  // NaN != 0
+    }
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kBlock)
 norm2_kernel(int vh, const R *__restrict__ f, double *out, CgScalars *S, double *partials, unsigned int *counter) {
@@ -265,6 +274,12 @@ qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, con
                             const GraphCtl &ctl, cudaStream_t st) {
     finish_ru_kernel<<<r32 ? blas_blocks(lat) : 1, kBlock, 0, st>>>((int)lat->vh, r64, r32, S, ctl);
     QEX_CHECK_LAUNCH("finish_ru_kernel");
+    return QEX_OK;
+}
+
+qex_status launch_any_nonzero(qex_lattice *lat, const double *f, int *flag, cudaStream_t st) {
+    any_nonzero_kernel<<<blas_blocks(lat), kBlock, 0, st>>>((size_t)lat->vh * 3, (const double2 *)f, flag);
+    QEX_CHECK_LAUNCH("any_nonzero_kernel");
     return QEX_OK;
 }
 

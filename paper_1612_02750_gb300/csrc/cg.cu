@@ -126,8 +126,10 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
 }
 
 // FP64 true residual r64 = b - A x64 (after folding x_hat into x64), then the
-// inner residual from it.
-static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStream_t st) {
+// inner residual from it.  `first`: the residual of the initial guess, whose
+// two Dslash passes do nothing when every element of x is zero (checked just
+// before).
+static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStream_t st, bool first = false) {
     qex_lattice *lat = s.lat;
     CgScalars *S = lat->scalars;
     qex_status err;
@@ -141,6 +143,8 @@ static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStr
     a.in = s.x64;
     a.out = s.B.tmp64;
     a.epi = EPI_PLAIN;
+    a.S = S;
+    a.skip_zero_x = first ? 1 : 0;
     if ((err = launch_dslash(lat, a, st))) return err;
     a.out_parity = 0;
     a.in = s.B.tmp64;
@@ -344,7 +348,8 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     if (mixed) QEX_CUDA(cudaMemsetAsync(s.B.xh32, 0, fbytes, cst));
     const GraphCtl off = {};
     if ((st = launch_norm2(lat, QEX_F64, b64, nullptr, lat->scalars, cst))) return st;
-    if ((st = enqueue_reliable_update(s, off, cst))) return st;
+    if ((st = launch_any_nonzero(lat, (const double *)x64, &lat->scalars->x_nonzero, cst))) return st;
+    if ((st = enqueue_reliable_update(s, off, cst, true))) return st;
     if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
 
     qex_status result = QEX_OK;

@@ -32,6 +32,7 @@ struct DsParams {
     const R *r;         // EPI_PUPD
     R *pbuf0, *pbuf1;   // p ping-pong
     int psel;
+    int skip_zero_x;
     double *partials;
     unsigned int *counter;
 };
@@ -41,6 +42,9 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     __shared__ double smem[32];
     __shared__ unsigned int is_last;
     if (P.check_halt && P.S->halt) return;  // uniform over the grid
+    // first residual from a zero initial guess: D x = 0 (uniform over the grid)
+    const bool zero_x = P.skip_zero_x && !P.S->x_nonzero;
+    if (EPI == EPI_PLAIN && zero_x) return;
 
     const Geom &g = P.g;
     const size_t vh = (size_t)g.vh;
@@ -62,12 +66,18 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     // the lattice, several when the launch is persistent (reducing variants)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += gridDim.x * blockDim.x) {
         const Site s = site_of(g, p, i);
-        const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, P.fat, P.lng, P.c3, p, i, s, [&](int j) {
-            if constexpr (EPI == EPI_PUPD)
-                return axpy_vec(P.r, pold, beta, vh, j);
-            else
-                return load_vec(in, vh, j);
-        });
+        Vec3<R> acc;
+        if (EPI == EPI_RESID && zero_x) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = R(0);
+        } else {
+            acc = dslash_site<R, FMT, NAIK>(g, P.fat, P.lng, P.c3, p, i, s, [&](int j) {
+                if constexpr (EPI == EPI_PUPD)
+                    return axpy_vec(P.r, pold, beta, vh, j);
+                else
+                    return load_vec(in, vh, j);
+            });
+        }
         if constexpr (EPI == EPI_PLAIN) {
             store_vec(P.out, vh, i, acc);
         } else if constexpr (EPI == EPI_PUPD) {
@@ -161,7 +171,8 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
 // fence-and-atomic tail once.
 static int dslash_grid(const qex_lattice *lat, bool reducing, int min_blocks) {
     const int full = blocks_for(lat->vh, kDslashBlock);
-    if (!reducing) return full;
+    if (QEX_REDUCE_BLOCKS_PER_SM >= 0) min_blocks = QEX_REDUCE_BLOCKS_PER_SM;
+    if (!reducing || min_blocks == 0) return full;
     const int persistent = sm_count() * min_blocks;
     return full < persistent ? full : persistent;
 }
@@ -185,6 +196,7 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.pbuf0 = (R *)a.pbuf[0];
     P.pbuf1 = (R *)a.pbuf[1];
     P.psel = a.psel;
+    P.skip_zero_x = a.skip_zero_x;
     P.partials = lat->partials;
     P.counter = lat->counter;
     dslash_kernel<R, FMT, NAIK, EPI><<<dslash_grid(lat, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr,

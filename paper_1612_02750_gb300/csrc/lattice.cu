@@ -75,7 +75,8 @@ int sm_count() {
 
 int blas_blocks(const qex_lattice *lat) {
     int want = blocks_for(lat->vh);
-    int cap = sm_count() * 8;
+    if (QEX_BLAS_BLOCKS_PER_SM <= 0) return want;
+    int cap = sm_count() * QEX_BLAS_BLOCKS_PER_SM;
     return want < cap ? want : cap;
 }
 

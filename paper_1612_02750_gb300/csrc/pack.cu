@@ -82,7 +82,8 @@ __device__ __forceinline__ void get_link(R12c base, size_t vh, int blk, int i, d
 }
 
 // Two-row links in 16-bit fixed point (q = round(v * 32767), v clamped to
-// [-1, 1]); elements 0..3 in a 16-byte word, 4..5 in an 8-byte word.
+// [-1, 1]), each re/im stored as the offset-binary u = q + 32768; elements
+// 0..3 in a 16-byte word, 4..5 in an 8-byte word.
 struct R12H {
     float *p;
 };
@@ -93,11 +94,11 @@ struct R12Hc {
 __device__ __forceinline__ uint32_t fix16_pair(double re, double im) {
     const double lo = fmin(1.0, fmax(-1.0, re)), hi = fmin(1.0, fmax(-1.0, im));
     const int qr = __double2int_rn(lo * 32767.0), qi = __double2int_rn(hi * 32767.0);
-    return (uint32_t)(qr & 0xFFFF) | ((uint32_t)(qi & 0xFFFF) << 16);
+    return (uint32_t)(qr + 32768) | ((uint32_t)(qi + 32768) << 16);
 }
 
 __device__ __forceinline__ double fix16_value(uint32_t w, bool hi) {
-    const int16_t q = (int16_t)(hi ? (w >> 16) : (w & 0xFFFFu));
+    const int q = (int)(hi ? (w >> 16) : (w & 0xFFFFu)) - 32768;
     return (double)q / 32767.0;
 }
 

@@ -207,19 +207,28 @@ __device__ __forceinline__ Mat3<float> load_link_r12(const float *base, size_t v
 }
 
 // Two-row links in 16-bit fixed point: block (p, mu) holds a plane of 16-byte
-// words (int16 re/im of elements 0..3) then a plane of 8-byte words
-// (elements 4, 5); block size 24*Vh bytes.  value = q / 32767.
-constexpr float kFix16Scale = 1.0f / 32767.0f;
+// words (re/im of elements 0..3) then a plane of 8-byte words (elements 4,
+// 5); block size 24*Vh bytes.  Each 32-bit word holds re in its low and im in
+// its high 16 bits as offset binary, u = q + 32768 with q = round(32767 v).
+//
+// The kernels decode the integer q, not q/32767: the 16 bits placed under the
+// exponent of 2^23 (one LOP3 or PRMT) give the float 2^23 + u exactly, and
+// subtracting 2^23 + 2^15 leaves q exactly.  The matrix they hold is then
+// 32767 U in rows 0, 1 and, rebuilt from those, 32767^2 U in row 2; the
+// scale comes back once per output row in the sign factor of the hop
+// (acc_mv_fix16, acc_mdv_fix16).
+constexpr float kFix16Inv = 1.0f / 32767.0f;
+constexpr float kFix16Inv2 = (float)(1.0 / (32767.0 * 32767.0));
 
-// int16 q in the low (hi = false) or high half of w -> q/32767: the 16 bits,
-// offset by 2^15, become the low mantissa bits of the float 2^23 + 2^15 + q
-// (one LOP3); subtracting 2^23 + 2^15 is exact, so q/32767 is rounded once.
-__device__ __forceinline__ float fix16_half(uint32_t w, bool hi) {
-    const uint32_t u = (hi ? (w >> 16) : (w & 0xFFFFu)) ^ 0x4B008000u;
-    return (__uint_as_float(u) - 8421376.0f) * kFix16Scale;
+__device__ __forceinline__ float fix16_lo(uint32_t w) {
+    return __uint_as_float((w & 0xFFFFu) | 0x4B000000u) - 8421376.0f;
+}
+__device__ __forceinline__ float fix16_hi(uint32_t w) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7632)) - 8421376.0f;
 }
 
-__device__ __forceinline__ Mat3<float> load_link_r12h(const float *base_f, size_t vh, int p, int mu, int i) {
+// 32767 x (rows 0, 1) and 32767^2 x (row 2) of the stored link.
+__device__ __forceinline__ Mat3<float> load_link_fix16(const float *base_f, size_t vh, int p, int mu, int i) {
     const char *blk = reinterpret_cast<const char *>(base_f) + (size_t)(p * 4 + mu) * 24 * vh;
     const uint4 a = __ldg(reinterpret_cast<const uint4 *>(blk) + i);
     const uint2 b = __ldg(reinterpret_cast<const uint2 *>(blk + 16 * vh) + i);
@@ -227,8 +236,8 @@ __device__ __forceinline__ Mat3<float> load_link_r12h(const float *base_f, size_
     Mat3<float> m;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        m.e[c].re = fix16_half(w[c], false);
-        m.e[c].im = fix16_half(w[c], true);
+        m.e[c].re = fix16_lo(w[c]);
+        m.e[c].im = fix16_hi(w[c]);
     }
     reconstruct_row2(m);
     return m;
@@ -289,6 +298,53 @@ __device__ __forceinline__ void acc_mv(Vec3<R> &acc, R sgn, const Mat3<R> &m, co
         }
         acc.c[a].re = fma(sgn, re, acc.c[a].re);
         acc.c[a].im = fma(sgn, im, acc.c[a].im);
+    }
+}
+
+// acc += sgn * (U v) for U held as load_link_fix16 returns it.
+__device__ __forceinline__ void acc_mv_fix16(Vec3<float> &acc, float sgn, const Mat3<float> &m, const Vec3<float> &v) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float re = m.e[3 * a].re * v.c[0].re;
+        float im = m.e[3 * a].re * v.c[0].im;
+        re = fmaf(-m.e[3 * a].im, v.c[0].im, re);
+        im = fmaf(m.e[3 * a].im, v.c[0].re, im);
+#pragma unroll
+        for (int b = 1; b < 3; ++b) {
+            re = fmaf(m.e[3 * a + b].re, v.c[b].re, re);
+            re = fmaf(-m.e[3 * a + b].im, v.c[b].im, re);
+            im = fmaf(m.e[3 * a + b].re, v.c[b].im, im);
+            im = fmaf(m.e[3 * a + b].im, v.c[b].re, im);
+        }
+        const float s = sgn * (a < 2 ? kFix16Inv : kFix16Inv2);
+        acc.c[a].re = fmaf(s, re, acc.c[a].re);
+        acc.c[a].im = fmaf(s, im, acc.c[a].im);
+    }
+}
+
+// acc += sgn * (U^+ v) for U held as load_link_fix16 returns it: column a of
+// U^+ mixes rows 0, 1 (scale 32767) with row 2 (scale 32767^2), so v_2 takes
+// one factor 1/32767 first and the row sign the other.
+__device__ __forceinline__ void acc_mdv_fix16(Vec3<float> &acc, float sgn, const Mat3<float> &m, const Vec3<float> &v) {
+    Vec3<float> w = v;
+    w.c[2].re *= kFix16Inv;
+    w.c[2].im *= kFix16Inv;
+    const float s = sgn * kFix16Inv;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float re = m.e[a].re * w.c[0].re;
+        float im = m.e[a].re * w.c[0].im;
+        re = fmaf(m.e[a].im, w.c[0].im, re);
+        im = fmaf(-m.e[a].im, w.c[0].re, im);
+#pragma unroll
+        for (int b = 1; b < 3; ++b) {
+            re = fmaf(m.e[3 * b + a].re, w.c[b].re, re);
+            re = fmaf(m.e[3 * b + a].im, w.c[b].im, re);
+            im = fmaf(m.e[3 * b + a].re, w.c[b].im, im);
+            im = fmaf(-m.e[3 * b + a].im, w.c[b].re, im);
+        }
+        acc.c[a].re = fmaf(s, re, acc.c[a].re);
+        acc.c[a].im = fmaf(s, im, acc.c[a].im);
     }
 }
 
@@ -392,6 +448,15 @@ constexpr int kBlock = 256;  // threads per block of the site kernels
 #endif
 #ifndef QEX_DSLASH_MIN_BLOCKS_F64
 #define QEX_DSLASH_MIN_BLOCKS_F64 3
+#endif
+// Grid of the reducing Dslash variants: resident blocks per SM of their
+// persistent grid (-1: the launch-bounds minimum; 0: one thread per site).
+#ifndef QEX_REDUCE_BLOCKS_PER_SM
+#define QEX_REDUCE_BLOCKS_PER_SM -1
+#endif
+// Cap of the streaming BLAS kernels' grid, in blocks per SM (0: no cap).
+#ifndef QEX_BLAS_BLOCKS_PER_SM
+#define QEX_BLAS_BLOCKS_PER_SM 4
 #endif
 constexpr int kDslashBlock = QEX_DSLASH_BLOCK;
 constexpr int kDslashMinBlocks = QEX_DSLASH_MIN_BLOCKS;         // FP32 variants

@@ -7,13 +7,14 @@
 namespace qex {
 
 // Fat-link formats: 0 = full 3x3 in the field precision, 1 = FP32 two-row,
-// 2 = 16-bit fixed-point two-row (third row rebuilt in registers).
+// 2 = 16-bit fixed-point two-row (third row rebuilt in registers, the matrix
+// held scaled: see load_link_fix16).
 template <typename R, int FMT>
 __device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int mu, int i) {
     if constexpr (FMT == 1)
         return load_link_r12(base, vh, p, mu, i);
     else if constexpr (FMT == 2)
-        return load_link_r12h(base, vh, p, mu, i);
+        return load_link_fix16(base, vh, p, mu, i);
     else
         return load_link(base, vh, p, mu, i);
 }
@@ -35,12 +36,18 @@ __device__ __forceinline__ Vec3<R> dslash_site(const Geom &g, const R *fat, cons
         {   // + eta b U_mu(x) in(x + mu)
             const int j = hop_index(g, s, mu, 1);
             const Mat3<R> u = load_fat<R, FMT>(fat, vh, p, mu, i);
-            acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
+            if constexpr (FMT == 2)
+                acc_mv_fix16(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
+            else
+                acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
         }
         {   // - eta b U_mu(x - mu)^+ in(x - mu)
             const int j = hop_index(g, s, mu, -1);
             const Mat3<R> u = load_fat<R, FMT>(fat, vh, 1 - p, mu, j);
-            acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
+            if constexpr (FMT == 2)
+                acc_mdv_fix16(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
+            else
+                acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
         }
         if (NAIK) {
             const R e3 = c3 * eta;

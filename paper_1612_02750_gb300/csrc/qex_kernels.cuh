@@ -28,6 +28,7 @@ struct CgScalars {
     int error;        // 1: NaN/Inf in a reduction, 2: <p, Ap> <= 0
     int reliable_updates;
     int trips;        // executions of the update kernel (graph loop guard)
+    int x_nonzero;    // the initial guess has an element != 0 (or NaN); 0: the first residual is b
 };
 
 // Conditional-node handles of the CUDA-graph solve (active = 0 outside it).
@@ -64,6 +65,8 @@ struct DslashArgs {
     const void *r;       // EPI_PUPD
     void *pbuf[2];       // EPI_PUPD, and EPI_PLAIN / EPI_NORMAL when psel
     int psel;            // EPI_PLAIN: in = p_new; EPI_NORMAL: q = p_new
+    int skip_zero_x;     // EPI_PLAIN / EPI_RESID of the first residual: unless S->x_nonzero,
+                         // PLAIN writes nothing and RESID takes D in = 0 (r = b)
 };
 
 qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
@@ -120,6 +123,8 @@ qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream
 // loop condition = !halt when ctl.active.
 qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, const CgScalars *S,
                             const GraphCtl &ctl, cudaStream_t st);
+// *flag |= (some element of the FP64 half field f is not zero; NaN counts).
+qex_status launch_any_nonzero(qex_lattice *lat, const double *f, int *flag, cudaStream_t st);
 // ||f||^2 -> *out (FP64, fixed order); if S, also S->bb and S->stop2.
 qex_status launch_norm2(qex_lattice *lat, qex_prec prec, const void *f, double *out, CgScalars *S,
                         cudaStream_t st);

@@ -143,7 +143,9 @@ def test_fix16_links_roundtrip(q):
     assert np.abs(back[..., :2, :] - quant).max() <= 1e-15
     assert np.abs(back - u).max() <= 1e-4
     via = q.qex_convert_links(lat, "f64", q.qex_pack_links(lat, "f64", dev(u)), "f32r12h")
-    assert np.array_equal(host(via).view(np.uint32), host(h).view(np.uint32))  # raw bits (words are not floats)
+    words = host(h).view(np.uint32)
+    assert np.array_equal(host(via).view(np.uint32), words)  # raw bits (words are not floats)
+    assert (words & 0xFFFF).min() >= 1 and (words >> 16).min() >= 1  # offset binary: q + 32768, q >= -32767
 
 
 @pytest.mark.parametrize("dims", SHAPES)
@@ -304,6 +306,28 @@ def test_cg_edge_cases(q, oracle_mod):
     _, _, xb = _cg(q, S, "f32", 0.1, b)
     assert np.array_equal(xa, xb)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32r12h"])
+def test_cg_initial_guess_zero_and_one_site(q, oracle_mod, inner):
+    """The first residual skips its Dslash passes only for an all-zero guess:
+    a guess that is zero except for one tiny element (1e-300, whose square
+    underflows) still gets b - A x, and both solves meet the oracle's true
+    residual."""
+    dims = (6, 4, 4, 10)
+    m = 0.1
+    S = Setup(q, dims, False, seed=26)
+    b = S.psi.copy()
+    b[~fg.even_mask(dims)] = 0
+    st0, stats0, x0 = _cg(q, S, inner, m, b)
+    assert st0 == 0 and oracle_mod.true_residual(dims, S.u, b, x0, m) <= 1.05e-10
+    for val in (1e-300, 3.0):
+        guess = np.zeros_like(b)
+        guess[0, 0, 0, 0, 1] = val  # an even site (x + y + z + t = 0)
+        st, stats, x = _cg(q, S, inner, m, b, x0=guess)
+        tr = oracle_mod.true_residual(dims, S.u, b, x, m)
+        assert st == 0 and tr <= 1.05e-10, (val, tr)
+        assert stats["true_rel_resid"] == pytest.approx(tr, rel=1e-3, abs=1e-13)
 
 
 def test_device_argument_errors(q):
