@@ -172,7 +172,8 @@ def measured_peak():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_1612_02750_gb300/csrc/dslash.cu", "paper_1612_02750_gb300/csrc/qex_common.cuh"):
+    for rel in ("paper_1612_02750_gb300/csrc/dslash.cu", "paper_1612_02750_gb300/csrc/qex_common.cuh",
+                "paper_1612_02750_gb300/csrc/qex_dslash_site.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
