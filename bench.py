@@ -371,6 +371,7 @@ def run_native(args):
             "fp64": {"iters": st64["iters"], "true_rel_resid": st64["true_rel_resid"],
                      "solve_ms": round(st64["time_ms"], 3), "step_ms": round(fp64_ms, 3)},
             "dslash": dslash,
+            "launch_shapes": {INNER: q.qex_tune_info(lat, INNER), "f64": q.qex_tune_info(lat, "f64")},
         }
         print(json.dumps(line), flush=True)
     lat.close()

@@ -333,6 +333,36 @@ qex_status qex_cg_host(const qex_lattice *lat, qex_prec inner, const double *hos
                        double c_naik, double mass, const double *host_b, double *host_x, double tol, int maxiter,
                        double delta, void *stream, qex_cg_stats *stats);
 
+/* ---------------------------------------------------------- autotuner
+ * Launch shapes (threads per block and grid) of the Dslash variants and of the
+ * CG vector kernels.  The paper has no counterpart: this is a GPU launch-
+ * configuration search.  For (lat, prec, Naik iff lng != NULL) qex_tune times,
+ * with CUDA events on scratch fields it allocates and frees (about three half
+ * fields), the plain Dslash at 256, 128 and 64 threads per block, the
+ * normal-operator Dslash (which ends in a grid reduction) at a few block
+ * sizes and grids, and the CG vector update with its grid capped at 2, 4, 8
+ * or 16 blocks per SM; it keeps a shape only if it beats the compiled default
+ * by more than 2 %, and stores the result in the lattice, in a per-process
+ * cache keyed by (SM count, extents, boundary, prec, Naik) and, if the
+ * environment variable QEX_TUNE_CACHE names a file, appends it there.
+ * fat (and lng) are the link sets in prec's layout (read only).  The call
+ * synchronises the stream.  Errors: QEX_ERR_ARG (null fat, or the stream is
+ * being captured), QEX_ERR_ALIGN, QEX_ERR_SHAPE (Naik with an extent < 4),
+ * QEX_ERR_CUDA.
+ * qex_dslash, qex_normal_op and qex_cg tune on their first uncaptured call
+ * for a (prec, Naik) unless QEX_TUNE=0, taking the cache (file included) when
+ * it holds the key.  Per-site results do not depend on the shape; FP64 sums
+ * over blocks (CG reductions) are bit-reproducible for a given shape. */
+qex_status qex_tune(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, void *stream);
+
+/* Launch shapes in use for (lat, prec, naik != 0): out[0] Dslash threads per
+ * block, out[1] threads per block of the reducing Dslash variants, out[2] their
+ * persistent grid in blocks per SM (0: one thread per site), out[3] the
+ * vector kernels' grid cap in blocks per SM, out[4] where they came from (0
+ * compiled defaults, not tuned yet; 1 measured; 2 cache; 3 defaults kept by
+ * QEX_TUNE=0).  out is a host array of 5 ints.  Errors: QEX_ERR_ARG. */
+qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int naik, int *out);
+
 /* Number of kernels this library has launched in the calling process so far
  * (monotone counter, for accounting of the kernels in a timed region). */
 uint64_t qex_launch_count(void);

@@ -96,6 +96,8 @@ def load():
         "qex_dslash_mrhs": (i, [vp, i, vp, vp, d, i, i, vp, vp, vp]),
         "qex_cg_mrhs": (i, [vp, i, vp, vp, vp, vp, d, d, i, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_cg_batch": (i, [i, ctypes.POINTER(CgItem), i, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_tune": (i, [vp, i, vp, vp, vp]),
+        "qex_tune_info": (i, [vp, i, i, ip]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -114,8 +116,8 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_launch_count",
-            "qex_last_error", "qex_version"]
+            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_tune",
+            "qex_tune_info", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -441,6 +443,20 @@ def qex_cg_host(lat: Lattice, inner, host_fat, host_lng, c_naik: float, mass: fl
     if check:
         _check(st)
     return host_x, st, stats.as_dict()
+
+
+def qex_tune(lat: Lattice, prec, fat, lng=None, stream=None):
+    """Time the launch shapes for (lat, prec, Naik iff lng) and keep the best."""
+    _check(load().qex_tune(lat.handle, _prec(prec), _ptr(fat), _ptr(lng), _stream(stream)))
+
+
+def qex_tune_info(lat: Lattice, prec, naik: bool = False) -> dict:
+    """Launch shapes in use for (lat, prec, naik)."""
+    out = (ctypes.c_int * 5)()
+    _check(load().qex_tune_info(lat.handle, _prec(prec), 1 if naik else 0, out))
+    src = {0: "default", 1: "measured", 2: "cache", 3: "disabled"}
+    return {"dslash_block": out[0], "reduce_block": out[1], "reduce_blocks_per_sm": out[2],
+            "blas_blocks_per_sm": out[3], "source": src.get(out[4], str(out[4]))}
 
 
 def qex_launch_count() -> int:

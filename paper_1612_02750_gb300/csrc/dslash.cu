@@ -165,16 +165,27 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     }
 }
 
-// Grid of a Dslash launch: one thread per site, or, for the variants that end
-// in a grid reduction, a persistent grid of as many blocks per SM as the
+// Shape of a Dslash launch: one thread per site, or, for the variants that
+// end in a grid reduction, a persistent grid of as many blocks per SM as the
 // launch bounds keep resident, so that each block pays the reduction's
-// fence-and-atomic tail once.
-static int dslash_grid(const qex_lattice *lat, bool reducing, int min_blocks) {
-    const int full = blocks_for(lat->vh, kDslashBlock);
-    if (QEX_REDUCE_BLOCKS_PER_SM >= 0) min_blocks = QEX_REDUCE_BLOCKS_PER_SM;
-    if (!reducing || min_blocks == 0) return full;
-    const int persistent = sm_count() * min_blocks;
-    return full < persistent ? full : persistent;
+// fence-and-atomic tail once.  The autotuner may replace the block size and
+// the persistent grid per (precision, Naik) of the lattice.
+static void dslash_shape(const qex_lattice *lat, qex_prec prec, bool naik, bool reducing, int min_blocks, int *grid,
+                         int *block) {
+    const LaunchShape &sh = lat->shape[prec][naik ? 1 : 0];
+    int per_sm = QEX_REDUCE_BLOCKS_PER_SM >= 0 ? QEX_REDUCE_BLOCKS_PER_SM : min_blocks;
+    int b = kDslashBlock;
+    if (sh.red_block > 0) {
+        b = reducing ? sh.red_block : sh.ds_block;
+        per_sm = sh.red_per_sm;
+    }
+    *block = b;
+    const int full = blocks_for(lat->vh, b);
+    *grid = full;
+    if (reducing && per_sm > 0) {
+        const int persistent = sm_count() * per_sm;
+        if (persistent < full) *grid = persistent;
+    }
 }
 
 template <typename R, int FMT, bool NAIK, int EPI>
@@ -199,9 +210,10 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.skip_zero_x = a.skip_zero_x;
     P.partials = lat->partials;
     P.counter = lat->counter;
-    dslash_kernel<R, FMT, NAIK, EPI><<<dslash_grid(lat, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr,
-                                                   DslashMinBlocks<R>::value),
-                                       kDslashBlock, 0, st>>>(P);
+    int grid, block;
+    dslash_shape(lat, a.prec, NAIK, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr, DslashMinBlocks<R>::value,
+                 &grid, &block);
+    dslash_kernel<R, FMT, NAIK, EPI><<<grid, block, 0, st>>>(P);
 }
 
 template <typename R, int FMT, bool NAIK>
@@ -292,6 +304,8 @@ qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, co
         set_error("out_parity must be 0 or 1");
         return QEX_ERR_ARG;
     }
+    qex_lattice *l = const_cast<qex_lattice *>(lat);
+    if ((st = ensure_tuned(l, prec, fat, lng, as_stream(stream), false))) return st;
     DslashArgs a = {};
     a.prec = prec;
     a.fat = fat;
@@ -301,7 +315,7 @@ qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, co
     a.in = in;
     a.out = out;
     a.epi = EPI_PLAIN;
-    return launch_dslash(const_cast<qex_lattice *>(lat), a, as_stream(stream));
+    return launch_dslash(l, a, as_stream(stream));
 }
 
 qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, double c_naik,
@@ -314,6 +328,7 @@ qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat,
     }
     qex_lattice *l = const_cast<qex_lattice *>(lat);
     cudaStream_t s = as_stream(stream);
+    if ((st = ensure_tuned(l, prec, fat, lng, s, false))) return st;
     DslashArgs a = {};
     a.prec = prec;
     a.fat = fat;

@@ -75,8 +75,9 @@ int sm_count() {
 
 int blas_blocks(const qex_lattice *lat) {
     int want = blocks_for(lat->vh);
-    if (QEX_BLAS_BLOCKS_PER_SM <= 0) return want;
-    int cap = sm_count() * QEX_BLAS_BLOCKS_PER_SM;
+    const int per_sm = lat->blas_per_sm > 0 ? lat->blas_per_sm : QEX_BLAS_BLOCKS_PER_SM;
+    if (per_sm <= 0) return want;
+    int cap = sm_count() * per_sm;
     return want < cap ? want : cap;
 }
 
@@ -85,8 +86,9 @@ int blas_blocks(const qex_lattice *lat) {
 // and the CG scalars with their pinned host mirror.
 qex_status ensure_scratch(qex_lattice *lat) {
     if (lat->partials) return QEX_OK;
-    int nb = blocks_for(lat->vh, kDslashBlock < kBlock ? kDslashBlock : kBlock);
-    int nbb = blas_blocks(lat);
+    // the largest grids any launch shape of the autotuner can give
+    int nb = blocks_for(lat->vh, 64);
+    int nbb = sm_count() * 16;
     lat->partials_len = 2 * (nb > nbb ? nb : nbb);
     const int mrhs = (sm_count() * 8 + 1) * kMaxRhs;  // per-block, per-right-hand-side partials
     if (lat->partials_len < mrhs) lat->partials_len = mrhs;

@@ -400,6 +400,14 @@ __device__ __forceinline__ double block_sum_partials(const double *partial, int 
 // ------------------------------------------------------- lattice object
 struct CgScalars;
 
+// Launch shapes of one (precision, Naik) of a lattice, chosen by the
+// autotuner (tune.cu); zeros mean the compiled defaults.
+struct LaunchShape {
+    int ds_block;    // threads per block of the non-reducing Dslash variants
+    int red_block;   // threads per block of the reducing variants (0: defaults for both fields)
+    int red_per_sm;  // their persistent grid, blocks per SM (0: one thread per site)
+};
+
 }  // namespace qex
 
 struct qex_lattice {
@@ -424,12 +432,21 @@ struct qex_lattice {
     void *cg_graph;            // cached CUDA graph of the last CG solve
     void *batch_ctx;           // scratch of qex_cg_batch calls led by this lattice
     cudaEvent_t ev0, ev1;
+    // autotuner state (tune.cu): per precision and Naik, and the BLAS grid
+    qex::LaunchShape shape[4][2];
+    int tuned[4][2];           // 0 no, 1 measured, 2 from the cache, 3 defaults (QEX_TUNE=0)
+    int blas_per_sm;           // 0: QEX_BLAS_BLOCKS_PER_SM
 };
 
 namespace qex {
 
 qex_status ensure_scratch(qex_lattice *lat);
 qex_status ensure_work(qex_lattice *lat, size_t bytes);
+// Tune (prec, Naik iff lng) of the lattice once, from the process cache or by
+// measurement on the stream (skipped while the stream is capturing).
+// tune_blas: also choose the BLAS grid from prec's vector-update kernel.
+qex_status ensure_tuned(qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, cudaStream_t st,
+                        bool tune_blas);
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 qex_status check_lattice(const qex_lattice *lat);

@@ -1,0 +1,350 @@
+// tune.cu -- launch-shape autotuner for the Dslash variants and the CG vector
+// kernels.
+//
+// The kernels are compiled for at most 256 threads per block with a register
+// cap that keeps a fixed number of threads resident per SM, so the block size
+// and the grid are free at launch time.  The best shape depends on the volume
+// (a small lattice wants small blocks to reach more SMs; the reducing
+// variants want a persistent grid whose per-block reduction tail is paid once)
+// and is measured, not guessed: for one (precision, Naik) of a lattice the
+// tuner times, with CUDA events on scratch fields,
+//   * the plain Dslash with 256, 128 and 64 threads per block,
+//   * the normal-operator Dslash (grid reduction) with a few (block, blocks
+//     per SM) pairs, the persistent grid and one thread per site among them,
+//   * optionally the CG vector update with its grid capped at 2, 4, 8 or 16
+//     blocks per SM,
+// and keeps a candidate only if it beats the compiled default by more than
+// 2 %.  Results are cached per process, keyed by (SM count, extents,
+// boundary, precision, Naik), and in the text file named by QEX_TUNE_CACHE
+// if set (one "qex-tune-v1" line per key).  QEX_TUNE=0 keeps the defaults.
+//
+// Launch shapes change only how sites are spread over threads: every per-site
+// result is unchanged, while FP64 sums over blocks (the CG reductions) are
+// bit-reproducible for a given shape.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "qex_kernels.cuh"
+
+namespace qex {
+
+qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
+
+namespace {
+
+struct TuneRecord {
+    LaunchShape shape;
+    int blas_per_sm;  // 0: not tuned with this record
+};
+
+std::mutex g_mu;
+std::map<std::string, TuneRecord> g_cache;
+bool g_file_loaded = false;
+
+std::string key_of(const qex_lattice *lat, qex_prec prec, int naik) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "sm%d dims%dx%dx%dx%d ap%d prec%d naik%d", sm_count(), lat->dims[0], lat->dims[1],
+             lat->dims[2], lat->dims[3], lat->antiperiodic, (int)prec, naik);
+    return buf;
+}
+
+// "qex-tune-v1 <key with spaces> | ds red per_sm blas"
+void load_file_locked() {
+    if (g_file_loaded) return;
+    g_file_loaded = true;
+    const char *path = getenv("QEX_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        if (strncmp(line, "qex-tune-v1 ", 12) != 0) continue;
+        char *bar = strchr(line, '|');
+        if (!bar) continue;
+        TuneRecord r;
+        memset(&r, 0, sizeof(r));
+        if (sscanf(bar + 1, "%d %d %d %d", &r.shape.ds_block, &r.shape.red_block, &r.shape.red_per_sm,
+                   &r.blas_per_sm) != 4)
+            continue;
+        const bool ok_block = [](int b) { return b == 64 || b == 128 || b == 256; }(r.shape.ds_block) &&
+                              (r.shape.red_block == 64 || r.shape.red_block == 128 || r.shape.red_block == 256);
+        if (!ok_block || r.shape.red_per_sm < 0 || r.shape.red_per_sm > 16 || r.blas_per_sm < 0 ||
+            r.blas_per_sm > 16)
+            continue;
+        std::string key(line + 12, bar - (line + 12));
+        while (!key.empty() && key.back() == ' ') key.pop_back();
+        g_cache[key] = r;
+    }
+    fclose(f);
+}
+
+void append_file_locked(const std::string &key, const TuneRecord &r) {
+    const char *path = getenv("QEX_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "qex-tune-v1 %s | %d %d %d %d\n", key.c_str(), r.shape.ds_block, r.shape.red_block,
+            r.shape.red_per_sm, r.blas_per_sm);
+    fclose(f);
+}
+
+bool tuning_enabled() {
+    const char *e = getenv("QEX_TUNE");
+    return !(e && strcmp(e, "0") == 0);
+}
+
+// Average time of one launch, in microseconds: two warm-up launches, then
+// enough to cover about half a millisecond (3 to 50).
+template <typename F>
+qex_status time_us(F launch, cudaStream_t st, float *us) {
+    cudaEvent_t a, b;
+    QEX_CUDA(cudaEventCreate(&a));
+    QEX_CUDA(cudaEventCreate(&b));
+    qex_status s = QEX_OK;
+    float ms = 0.f;
+    int reps = 3;
+    for (int pass = 0; pass < 2 && !s; ++pass) {
+        if (pass == 0) {
+            for (int k = 0; k < 2 && !s; ++k) s = launch();
+        }
+        if (s) break;
+        cudaEventRecord(a, st);
+        for (int k = 0; k < reps && !s; ++k) s = launch();
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            s = cuda_fail(cudaGetLastError(), "timing a launch shape");
+            break;
+        }
+        cudaEventElapsedTime(&ms, a, b);
+        const float per = ms * 1e3f / reps;
+        if (pass == 0) {
+            int want = per > 0.f ? (int)(500.f / per) : 50;
+            reps = want < 3 ? 3 : (want > 50 ? 50 : want);
+        } else {
+            *us = per;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return s;
+}
+
+// Measure and set lat->shape[prec][naik] (and lat->blas_per_sm if tune_blas).
+qex_status measure(qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, cudaStream_t st,
+                   bool tune_blas, TuneRecord *out) {
+    const int naik = lng ? 1 : 0;
+    const size_t fb = (size_t)lat->vh * (prec == QEX_F64 ? 48 : 24);
+    char *f = nullptr;
+    CgScalars *S = nullptr;
+    qex_status s = QEX_OK;
+    if (cudaMalloc(&f, 3 * fb) != cudaSuccess || cudaMalloc(&S, sizeof(CgScalars)) != cudaSuccess) {
+        cudaFree(f);
+        return cuda_fail(cudaGetLastError(), "allocating the autotuner's scratch fields");
+    }
+    // finite, nonzero contents (the byte 0x3C repeated: ~0.0115 as float, ~1.5e-18 as double)
+    cudaMemsetAsync(f, 0x3C, 3 * fb, st);
+    CgScalars init;
+    memset(&init, 0, sizeof(init));
+    init.rr = 1.0;
+    init.stop2 = -1.0;  // the update kernel never asks for a reliable update
+    init.maxiter = 0x7FFFFFFF;
+    auto reset_S = [&]() { cudaMemcpyAsync(S, &init, sizeof(init), cudaMemcpyHostToDevice, st); };
+    reset_S();
+    void *f0 = f, *f1 = f + fb, *f2 = f + 2 * fb;
+    LaunchShape &cur = lat->shape[prec][naik];
+    const LaunchShape saved = cur;
+    const int saved_blas = lat->blas_per_sm;
+    const int minb = prec == QEX_F64 ? kDslashMinBlocksF64 : kDslashMinBlocks;
+    const int def_per_sm = QEX_REDUCE_BLOCKS_PER_SM >= 0 ? QEX_REDUCE_BLOCKS_PER_SM : minb;
+    TuneRecord best;
+    memset(&best, 0, sizeof(best));
+    best.shape.ds_block = kDslashBlock;
+    best.shape.red_block = kDslashBlock;
+    best.shape.red_per_sm = def_per_sm;
+
+    DslashArgs a = {};
+    a.prec = prec;
+    a.fat = fat;
+    a.lng = lng;
+    a.c3 = lng ? -1.0 / 24.0 : 0.0;
+    a.m2 = 0.01;
+    do {
+        // plain Dslash: block size
+        a.epi = EPI_PLAIN;
+        a.out_parity = 1;
+        a.in = f0;
+        a.out = f1;
+        a.S = nullptr;
+        float t_best = 0.f;
+        const int blocks[3] = {256, 128, 64};
+        for (int k = 0; k < 3 && !s; ++k) {
+            cur.ds_block = blocks[k];
+            cur.red_block = kDslashBlock;
+            cur.red_per_sm = def_per_sm;
+            float t = 0.f;
+            s = time_us([&] { return launch_dslash(lat, a, st); }, st, &t);
+            if (!s && (k == 0 || t < 0.98f * t_best)) {
+                t_best = t;
+                best.shape.ds_block = blocks[k];
+            }
+        }
+        if (s) break;
+        // normal-operator Dslash with its grid reduction: block and grid
+        a.epi = EPI_NORMAL;
+        a.out_parity = 0;
+        a.in = f1;
+        a.out = f2;
+        a.q = f0;
+        a.S = S;
+        const int cand[5][2] = {{256, def_per_sm}, {256, 0}, {128, 2 * minb}, {128, minb}, {64, 4 * minb}};
+        for (int k = 0; k < 5 && !s; ++k) {
+            cur.ds_block = best.shape.ds_block;
+            cur.red_block = cand[k][0];
+            cur.red_per_sm = cand[k][1];
+            float t = 0.f;
+            s = time_us([&] { return launch_dslash(lat, a, st); }, st, &t);
+            if (!s && (k == 0 || t < 0.98f * t_best)) {
+                t_best = t;
+                best.shape.red_block = cand[k][0];
+                best.shape.red_per_sm = cand[k][1];
+            }
+        }
+        if (s) break;
+        cur = best.shape;
+        if (tune_blas) {
+            // the CG vector update (x += alpha p, r -= alpha A p, ||r||^2) in prec
+            const int caps[4] = {QEX_BLAS_BLOCKS_PER_SM > 0 ? QEX_BLAS_BLOCKS_PER_SM : 4, 2, 8, 16};
+            void *pb[2] = {f2, f2};
+            const GraphCtl off = {};
+            for (int k = 0; k < 4 && !s; ++k) {
+                if (k > 0 && caps[k] == caps[0]) continue;
+                lat->blas_per_sm = caps[k];
+                reset_S();
+                float t = 0.f;
+                s = time_us([&] { return launch_update_xr(lat, prec, f0, f1, pb, f2, S, off, st); }, st, &t);
+                if (!s && (k == 0 || t < 0.98f * t_best)) {
+                    t_best = t;
+                    best.blas_per_sm = caps[k];
+                }
+            }
+        }
+    } while (0);
+    cudaStreamSynchronize(st);
+    cudaFree(f);
+    cudaFree(S);
+    if (s) {
+        cur = saved;
+        lat->blas_per_sm = saved_blas;
+        return s;
+    }
+    cur = best.shape;
+    lat->blas_per_sm = tune_blas ? best.blas_per_sm : saved_blas;
+    *out = best;
+    return QEX_OK;
+}
+
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // do not synchronise a stream we cannot inspect
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+qex_status tune(qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, cudaStream_t st, bool tune_blas,
+                bool force) {
+    const int naik = lng ? 1 : 0;
+    if (!force && lat->tuned[prec][naik]) return QEX_OK;
+    if (!force && !tuning_enabled()) {
+        lat->tuned[prec][naik] = 3;
+        return QEX_OK;
+    }
+    if (capturing(st)) return QEX_OK;  // defaults for now; tuned at a later uncaptured call
+    const std::string key = key_of(lat, prec, naik);
+    if (!force) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_file_locked();
+        auto it = g_cache.find(key);
+        if (it != g_cache.end() && (!tune_blas || it->second.blas_per_sm > 0)) {
+            lat->shape[prec][naik] = it->second.shape;
+            if (tune_blas) lat->blas_per_sm = it->second.blas_per_sm;
+            lat->tuned[prec][naik] = 2;
+            return QEX_OK;
+        }
+    }
+    qex_status s = ensure_scratch(lat);
+    if (s) return s;
+    if (lat->cg_graph) {  // its kernels carry the old launch shapes
+        cudaStreamSynchronize(st);
+        free_cg_graph(lat->cg_graph);
+        lat->cg_graph = nullptr;
+    }
+    TuneRecord r;
+    if ((s = measure(lat, prec, fat, lng, st, tune_blas, &r))) return s;
+    lat->tuned[prec][naik] = 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_file_locked();
+    auto it = g_cache.find(key);
+    if (!tune_blas && it != g_cache.end()) r.blas_per_sm = it->second.blas_per_sm;
+    g_cache[key] = r;
+    append_file_locked(key, r);
+    return QEX_OK;
+}
+
+}  // namespace
+
+qex_status ensure_tuned(qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, cudaStream_t st,
+                        bool tune_blas) {
+    return tune(lat, prec, fat, lng, st, tune_blas, false);
+}
+
+}  // namespace qex
+
+using namespace qex;
+
+extern "C" qex_status qex_tune(const qex_lattice *latc, qex_prec prec, const void *fat, const void *lng,
+                               void *stream) {
+    qex_status st;
+    if ((st = check_lattice(latc)) || (st = check_prec(prec))) return st;
+    if (!fat || !aligned16(fat) || (lng && !aligned16(lng))) {
+        set_error("fat must be non-NULL; links must be 16-byte aligned");
+        return fat ? QEX_ERR_ALIGN : QEX_ERR_ARG;
+    }
+    if (lng) {
+        for (int mu = 0; mu < 4; ++mu)
+            if (latc->dims[mu] < 4) {
+                set_error("the Naik term needs every extent >= 4");
+                return QEX_ERR_SHAPE;
+            }
+    }
+    const cudaStream_t s = as_stream(stream);
+    if (capturing(s)) {
+        set_error("qex_tune cannot run while the stream is being captured");
+        return QEX_ERR_ARG;
+    }
+    return tune(const_cast<qex_lattice *>(latc), prec, fat, lng, s, true, true);
+}
+
+extern "C" qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int naik, int *out) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(prec))) return st;
+    if (!out) {
+        set_error("out must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    const LaunchShape &sh = lat->shape[prec][naik ? 1 : 0];
+    const int minb = prec == QEX_F64 ? kDslashMinBlocksF64 : kDslashMinBlocks;
+    const bool set = sh.red_block > 0;
+    out[0] = set ? sh.ds_block : kDslashBlock;
+    out[1] = set ? sh.red_block : kDslashBlock;
+    out[2] = set ? sh.red_per_sm : (QEX_REDUCE_BLOCKS_PER_SM >= 0 ? QEX_REDUCE_BLOCKS_PER_SM : minb);
+    out[3] = lat->blas_per_sm > 0 ? lat->blas_per_sm : QEX_BLAS_BLOCKS_PER_SM;
+    out[4] = lat->tuned[prec][naik ? 1 : 0];
+    return QEX_OK;
+}

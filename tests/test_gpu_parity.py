@@ -143,6 +143,13 @@ def test_fix16_links_roundtrip(q):
     assert np.abs(back[..., :2, :] - quant).max() <= 1e-15
     assert np.abs(back - u).max() <= 1e-4
     via = q.qex_convert_links(lat, "f64", q.qex_pack_links(lat, "f64", dev(u)), "f32r12h")
+    # entries outside [-1, 1] and NaN clamp to +-32767 (NaN to -32767)
+    v = u.copy()
+    v[0, 0, 0, 0, 0, 0, 0] = 1.5 - 2.5j
+    v[0, 0, 0, 0, 1, 0, 1] = complex(np.nan, 0.25)
+    hv = host(q.qex_unpack_links(lat, "f32r12h", q.qex_pack_links(lat, "f32r12h", dev(v))))
+    assert hv[0, 0, 0, 0, 0, 0, 0] == 1.0 - 1.0j
+    assert hv[0, 0, 0, 0, 1, 0, 1] == complex(-1.0, round(0.25 * 32767) / 32767)
     words = host(h).view(np.uint32)
     assert np.array_equal(host(via).view(np.uint32), words)  # raw bits (words are not floats)
     assert (words & 0xFFFF).min() >= 1 and (words >> 16).min() >= 1  # offset binary: q + 32768, q >= -32767
