@@ -37,7 +37,7 @@ DELTA = 0.01           # reliable-update threshold (sweep on this workload: same
 INNER = "f32r12h"      # inner CG precision: FP32 fields, two-row 16-bit fixed-point SU(3) links
 FLOP_NN = 570          # flops per output site of the one-hop Dslash (8 mat-vecs x 66 + 7 x 6 adds)
 # 8 links + 8 input vectors counted once + 1 output vector, per output site
-BYTES_NN = {"f64": 1248, "f32": 624, "f32r12": 432, "f32r12h": 240}
+BYTES_NN = {"f64": 1248, "f32": 624, "f32r12": 432, "f32r12h": 240, "f32s16": 368}
 L2_BYTES = 135528448   # sm_103a L2 (cudaDevAttrL2CacheSize on GB300)
 FALLBACK_HBM_GBS = 6800.0
 
@@ -454,7 +454,8 @@ def run_dslash_only():
 
 SWEEP_L = (8, 12, 16, 24, 32)
 SWEEP_T = (8, 12, 16, 24, 32, 48, 64)
-BYTES_NAIK = {"f64": 2400, "f32": 1200, "f32r12": 1008, "f32r12h": 816}  # 16 links + 16 in once + 1 out
+# 8 fat + 8 long links + the input vector once + 1 out; 16-bit formats read 40-byte long links
+BYTES_NAIK = {"f64": 2400, "f32": 1200, "f32r12": 1008, "f32r12h": 560, "f32s16": 688}
 FLOP_NAIK = 1146
 
 
@@ -478,8 +479,10 @@ def run_sweep(args):
         fat64 = torch.randn(q.qex_links_bytes(lat, "f64") // 8, dtype=torch.float64, device="cuda", generator=gen)
         lng64 = torch.randn_like(fat64)
         sets = {"f64": (fat64, lng64), "f32": (fat64.float(), lng64.float())}
+        lng16 = q.qex_convert_links(lat, "f64", lng64, "f32s16")
         sets["f32r12"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12"), sets["f32"][1])
-        sets["f32r12h"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12h"), sets["f32"][1])
+        sets["f32r12h"] = (q.qex_convert_links(lat, "f64", fat64, "f32r12h"), lng16)
+        sets["f32s16"] = (q.qex_convert_links(lat, "f64", fat64, "f32s16"), lng16)
         for prec, (fat, lng) in sets.items():
             inp = q.empty_field(lat, prec).normal_(generator=gen)
             out = q.empty_field(lat, prec)
@@ -514,14 +517,20 @@ def run_sweep(args):
         lng64 = q.qex_pack_links(lat, "f64", torch.from_numpy(w).cuda())
         del u, w
         torch.cuda.empty_cache()
-        fatr = q.qex_convert_links(lat, "f64", fat64, "f32r12")
-        lng32 = q.qex_convert_links(lat, "f64", lng64, "f32")
         bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
-        x = torch.zeros_like(bh)
-        st, stats = q.qex_cg(lat, "f32r12", fat64, lng64, fatr, lng32, -1.0 / 24, wl["mass"], bh, x, tol=TOL,
-                             maxiter=60000, delta=DELTA, check=False)  # Haar at m = 0.005: FP32 two-row inner
-        print(json.dumps({"sweep": "cg", "workload": "64^4 Naik, Haar fat links, Gaussian/sqrt(3) long links, "
-                          "c3=-1/24, m=0.005", "status": st, **stats}), flush=True)
+        # inner formats: FP32 two-row fat + FP32 long links, and 16-bit two-row fat + 16-bit scaled long
+        # links (Haar links at m = 0.005: delta 0.1 for the 16-bit inner solve, as on the 16^4 Haar study)
+        for inner, delta in (("f32r12", DELTA), ("f32r12h", 0.1)):
+            fati = q.qex_convert_links(lat, "f64", fat64, inner)
+            lngi = q.qex_convert_links(lat, "f64", lng64, q.qex_long_links_prec(inner))
+            x = torch.zeros_like(bh)
+            st, stats = q.qex_cg(lat, inner, fat64, lng64, fati, lngi, -1.0 / 24, wl["mass"], bh, x, tol=TOL,
+                                 maxiter=80000, delta=delta, check=False)
+            print(json.dumps({"sweep": "cg", "workload": "64^4 Naik, Haar fat links, Gaussian/sqrt(3) long links, "
+                              "c3=-1/24, m=0.005", "inner": inner, "long_links": q.qex_long_links_prec(inner),
+                              "delta": delta, "status": st, **stats}), flush=True)
+            del fati, lngi, x
+            torch.cuda.empty_cache()
 
 
 MRHS_MASS = 0.05  # the 16-source solve's mass (the workload names masses only for the multi-lattice case)

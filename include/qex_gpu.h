@@ -36,9 +36,11 @@
  *            of float4 (elements 0-1, 2-3, 4-5: rows 0 and 1); F32_R12H: 1
  *            plane of 16-byte words (elements 0-3) and 1 plane of 8-byte
  *            words (elements 4-5), one 32-bit word per element: re in the
- *            low, im in the high 16 bits.  Size qex_links_bytes().
+ *            low, im in the high 16 bits; F32_S16: 2 planes of 16-byte
+ *            words (elements 0-3, 4-7) and 1 plane of 8-byte words (element
+ *            8, then the FP32 step d).  Size qex_links_bytes().
  *     half field (the Vh sites of one parity): F64: 3 planes of double2
- *            (colour a); F32, F32_R12 and F32_R12H: 1 plane of float4
+ *            (colour a); every FP32 precision: 1 plane of float4
  *            (colours 0,1) + 1 plane of float2 (colour 2).  Size
  *            qex_field_bytes().
  * - All field and link pointers are caller-owned DEVICE memory, 16-byte
@@ -83,9 +85,15 @@ typedef enum {
  * as the unsigned offset-binary q + 32768; value q / 32767; SU(3) entries
  * lie in [-1, 1]), quantisation error <= 1.5e-5 per real: an inner-solver format
  * (use it inside mixed-precision CG, whose FP64 reliable updates correct
- * it).  Long (Naik) links are never compressed: with QEX_F32_R12 or
- * QEX_F32_R12H the long link set is in QEX_F32 format. */
-typedef enum { QEX_F64 = 0, QEX_F32 = 1, QEX_F32_R12 = 2, QEX_F32_R12H = 3 } qex_prec;
+ * it).  QEX_F32_S16 means FP32 fields and links of any kind (unitary or
+ * not) as all 18 reals in 16-bit fixed point with a per-link FP32 step d =
+ * (largest |re| or |im| of the link) / 32767 rounded up: q = round(v / d)
+ * (computed as v * (1/d)), value q * d, error <= d / 2 per real.
+ * Long (Naik) links have the format qex_long_links_prec(prec): QEX_F64 and
+ * QEX_F32 keep their own; QEX_F32_R12 uses QEX_F32 (long links are not
+ * unitary, so two-row storage does not apply); QEX_F32_R12H and QEX_F32_S16
+ * use QEX_F32_S16. */
+typedef enum { QEX_F64 = 0, QEX_F32 = 1, QEX_F32_R12 = 2, QEX_F32_R12H = 3, QEX_F32_S16 = 4 } qex_prec;
 
 typedef struct qex_lattice qex_lattice; /* opaque, owned by the library */
 
@@ -132,6 +140,10 @@ qex_status qex_neighbor_table_device(const qex_lattice *lat, int parity, int mu,
 /* Bytes of one internal link set (4V links) and of one internal half field. */
 size_t qex_links_bytes(const qex_lattice *lat, qex_prec prec);
 size_t qex_field_bytes(const qex_lattice *lat, qex_prec prec);
+
+/* Format of the long (Naik) link set that an operator of precision prec
+ * reads (see the precisions above); -1 for an unknown prec. */
+int qex_long_links_prec(qex_prec prec);
 
 /* Canonical lex links (complex double, [V][4][3][3]) -> internal links of
  * precision prec (F32 rounds to nearest).  lex_links and internal must not

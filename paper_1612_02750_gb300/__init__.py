@@ -27,9 +27,12 @@ F64 = 0
 F32 = 1
 F32_R12 = 2  # FP32 fields; FP32 SU(3) fat links stored as two rows
 F32_R12H = 3  # FP32 fields; SU(3) fat links as two rows of 16-bit fixed point
-_PREC = {"f64": F64, "f32": F32, "f32r12": F32_R12, "f32r12h": F32_R12H, F64: F64, F32: F32, F32_R12: F32_R12,
-         F32_R12H: F32_R12H, torch.float64: F64, torch.float32: F32}
-_DTYPE = {F64: torch.float64, F32: torch.float32, F32_R12: torch.float32, F32_R12H: torch.float32}
+F32_S16 = 4  # FP32 fields; links (any kind) as 16-bit fixed point with a per-link step
+_PREC = {"f64": F64, "f32": F32, "f32r12": F32_R12, "f32r12h": F32_R12H, "f32s16": F32_S16, F64: F64, F32: F32,
+         F32_R12: F32_R12, F32_R12H: F32_R12H, F32_S16: F32_S16, torch.float64: F64, torch.float32: F32}
+_NAMES = {F64: "f64", F32: "f32", F32_R12: "f32r12", F32_R12H: "f32r12h", F32_S16: "f32s16"}
+_DTYPE = {F64: torch.float64, F32: torch.float32, F32_R12: torch.float32, F32_R12H: torch.float32,
+          F32_S16: torch.float32}
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_ALIGN", 4: "ERR_CUDA",
            5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_NAN"}
 
@@ -96,6 +99,7 @@ def load():
         "qex_dslash_mrhs": (i, [vp, i, vp, vp, d, i, i, vp, vp, vp]),
         "qex_cg_mrhs": (i, [vp, i, vp, vp, vp, vp, d, d, i, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_cg_batch": (i, [i, ctypes.POINTER(CgItem), i, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_long_links_prec": (i, [i]),
         "qex_tune": (i, [vp, i, vp, vp, vp]),
         "qex_tune_info": (i, [vp, i, i, ip]),
         "qex_launch_count": (ctypes.c_uint64, []),
@@ -116,7 +120,8 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_tune",
+            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_long_links_prec",
+            "qex_tune",
             "qex_tune_info", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
@@ -443,6 +448,11 @@ def qex_cg_host(lat: Lattice, inner, host_fat, host_lng, c_naik: float, mass: fl
     if check:
         _check(st)
     return host_x, st, stats.as_dict()
+
+
+def qex_long_links_prec(prec) -> str:
+    """Name of the long-link format an operator of precision ``prec`` reads."""
+    return _NAMES[int(load().qex_long_links_prec(_prec(prec)))]
 
 
 def qex_tune(lat: Lattice, prec, fat, lng=None, stream=None):

@@ -493,6 +493,8 @@ static qex_status enqueue_iteration(const BatchLaunch &b, const GraphCtl &ctl, c
             launch_iter_n<float, 1>(b, role, s);
         else if (b.inner == QEX_F32_R12H)
             launch_iter_n<float, 2>(b, role, s);
+        else if (b.inner == QEX_F32_S16)
+            launch_iter_n<float, 3>(b, role, s);
         else
             launch_iter_n<float, 0>(b, role, s);
         QEX_CHECK_LAUNCH("batch_iter_dslash_kernel");

@@ -253,6 +253,11 @@ qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st)
                 launch_epi<float, 2, true>(lat, a, st);
             else
                 launch_epi<float, 2, false>(lat, a, st);
+        } else if (a.prec == QEX_F32_S16) {
+            if (a.lng)
+                launch_epi<float, 3, true>(lat, a, st);
+            else
+                launch_epi<float, 3, false>(lat, a, st);
         } else {
             if (a.lng)
                 launch_epi<float, 0, true>(lat, a, st);

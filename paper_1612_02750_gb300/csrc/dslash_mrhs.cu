@@ -265,6 +265,11 @@ qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t 
                 launch_m_epi<float, 2, true>(lat, a, st);
             else
                 launch_m_epi<float, 2, false>(lat, a, st);
+        } else if (a.prec == QEX_F32_S16) {
+            if (a.lng)
+                launch_m_epi<float, 3, true>(lat, a, st);
+            else
+                launch_m_epi<float, 3, false>(lat, a, st);
         } else {
             if (a.lng)
                 launch_m_epi<float, 0, true>(lat, a, st);

@@ -70,7 +70,9 @@ extern "C" qex_status qex_cg_host(const qex_lattice *latc, qex_prec inner, const
     if (naik) {
         QEX_CUDA(cudaMemcpyAsync(d_lex, host_lng, lex_links, cudaMemcpyHostToDevice, s));
         if ((st = qex_pack_links(lat, QEX_F64, d_lex, lng64, stream))) return st;
-        if (mixed && (st = qex_convert_links(lat, QEX_F64, lng64, QEX_F32, lng32, stream))) return st;
+        if (mixed && (st = qex_convert_links(lat, QEX_F64, lng64, (qex_prec)qex_long_links_prec(inner), lng32,
+                                                  stream)))
+            return st;
     }
     QEX_CUDA(cudaMemcpyAsync(d_field, host_b, lex_field, cudaMemcpyHostToDevice, s));
     if ((st = qex_pack_field(lat, QEX_F64, 0, d_field, b64, stream))) return st;

@@ -55,7 +55,7 @@ qex_status check_lattice(const qex_lattice *lat) {
 }
 
 qex_status check_prec(qex_prec prec) {
-    if (prec != QEX_F64 && prec != QEX_F32 && prec != QEX_F32_R12 && prec != QEX_F32_R12H) {
+    if (prec != QEX_F64 && prec != QEX_F32 && prec != QEX_F32_R12 && prec != QEX_F32_R12H && prec != QEX_F32_S16) {
         set_error("unknown precision %d", (int)prec);
         return QEX_ERR_ARG;
     }
@@ -260,7 +260,19 @@ size_t qex_links_bytes(const qex_lattice *lat, qex_prec prec) {
     if (!lat) return 0;
     if (prec == QEX_F32_R12) return (size_t)lat->volume * 4 * 12 * 4;
     if (prec == QEX_F32_R12H) return (size_t)lat->volume * 4 * 12 * 2;
+    if (prec == QEX_F32_S16) return (size_t)lat->volume * 4 * 40;
     return (size_t)lat->volume * 4 * 18 * (prec == QEX_F64 ? 8 : 4);
+}
+
+int qex_long_links_prec(qex_prec prec) {
+    switch (prec) {
+        case QEX_F64: return QEX_F64;
+        case QEX_F32:
+        case QEX_F32_R12: return QEX_F32;
+        case QEX_F32_R12H:
+        case QEX_F32_S16: return QEX_F32_S16;
+        default: return -1;
+    }
 }
 
 size_t qex_field_bytes(const qex_lattice *lat, qex_prec prec) {

@@ -95,10 +95,11 @@ struct R12Hc {
 // [-1, 1] first (both are monotonic; the conversion saturates, and a NaN
 // converts to INT_MIN, i.e. -32767 as with the clamp), with two FP64
 // operations per real instead of four.
-__device__ __forceinline__ int fix16_q(double v) {
-    const int q = __double2int_rn(v * 32767.0);
+__device__ __forceinline__ int fix16_round(double x) {
+    const int q = __double2int_rn(x);
     return q < -32767 ? -32767 : (q > 32767 ? 32767 : q);
 }
+__device__ __forceinline__ int fix16_q(double v) { return fix16_round(v * 32767.0); }
 
 __device__ __forceinline__ uint32_t fix16_pair(double re, double im) {
     return (uint32_t)(fix16_q(re) + 32768) | ((uint32_t)(fix16_q(im) + 32768) << 16);
@@ -135,6 +136,50 @@ __device__ __forceinline__ void get_link(R12Hc base, size_t vh, int blk, int i, 
         m[2 * k + 1] = u.e[k].im;
     }
 }
+
+// Full 3x3 links in 16-bit fixed point with a per-link FP32 step d: d is
+// the largest |re| or |im| of the link over 32767, rounded up to FP32 (so
+// every |v| / d <= 32767), and q = round(v * (1/d)) clamped to +-32767 (all
+// zero for a zero link).  Elements 0..3 and 4..7 in two 16-byte words,
+// element 8 and d in an 8-byte word.
+struct S16 {
+    float *p;
+};
+struct S16c {
+    const float *p;
+};
+
+__device__ __forceinline__ void put_link(S16 base, size_t vh, int blk, int i, const double *m) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) s = fmax(s, fabs(m[k]));
+    const float d = __double2float_ru(s / 32767.0);
+    const double inv = d > 0.f ? 1.0 / (double)d : 0.0;
+    uint32_t w[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        w[k] = (uint32_t)(fix16_round(m[2 * k] * inv) + 32768) |
+               ((uint32_t)(fix16_round(m[2 * k + 1] * inv) + 32768) << 16);
+    char *b = reinterpret_cast<char *>(base.p) + (size_t)blk * 40 * vh;
+    reinterpret_cast<uint4 *>(b)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4 *>(b + 16 * vh)[i] = make_uint4(w[4], w[5], w[6], w[7]);
+    reinterpret_cast<uint2 *>(b + 32 * vh)[i] = make_uint2(w[8], __float_as_uint(d));
+}
+
+__device__ __forceinline__ void get_link(S16c base, size_t vh, int blk, int i, double *m) {
+    const char *b = reinterpret_cast<const char *>(base.p) + (size_t)blk * 40 * vh;
+    const uint4 a = reinterpret_cast<const uint4 *>(b)[i];
+    const uint4 c = reinterpret_cast<const uint4 *>(b + 16 * vh)[i];
+    const uint2 e = reinterpret_cast<const uint2 *>(b + 32 * vh)[i];
+    const uint32_t w[9] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, e.x};
+    const double d = (double)__uint_as_float(e.y);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        m[2 * k] = (double)((int)(w[k] & 0xFFFFu) - 32768) * d;
+        m[2 * k + 1] = (double)((int)(w[k] >> 16) - 32768) * d;
+    }
+}
+
 
 __device__ __forceinline__ void put_vec(double *base, size_t vh, int i, const double *v) {
     double2 *b = reinterpret_cast<double2 *>(base) + i;
@@ -257,8 +302,10 @@ static void convert_links_to(qex_prec to, int vh, RI in, void *out, dim3 grid, c
         convert_links_kernel<RI, float *><<<grid, kBlock, 0, s>>>(vh, in, (float *)out);
     else if (to == QEX_F32_R12)
         convert_links_kernel<RI, R12><<<grid, kBlock, 0, s>>>(vh, in, R12{(float *)out});
-    else
+    else if (to == QEX_F32_R12H)
         convert_links_kernel<RI, R12H><<<grid, kBlock, 0, s>>>(vh, in, R12H{(float *)out});
+    else
+        convert_links_kernel<RI, S16><<<grid, kBlock, 0, s>>>(vh, in, S16{(float *)out});
 }
 
 }  // namespace qex
@@ -279,8 +326,10 @@ qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *l
         pack_links_kernel<float *><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, (float *)internal);
     else if (prec == QEX_F32_R12)
         pack_links_kernel<R12><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, R12{(float *)internal});
-    else
+    else if (prec == QEX_F32_R12H)
         pack_links_kernel<R12H><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, R12H{(float *)internal});
+    else
+        pack_links_kernel<S16><<<grid, kBlock, 0, s>>>(lat->geom, lex_links, S16{(float *)internal});
     QEX_CHECK_LAUNCH("pack_links_kernel");
     return QEX_OK;
 }
@@ -297,8 +346,10 @@ qex_status qex_unpack_links(const qex_lattice *lat, qex_prec prec, const void *i
         unpack_links_kernel<const float *><<<grid, kBlock, 0, s>>>(lat->geom, (const float *)internal, lex_links);
     else if (prec == QEX_F32_R12)
         unpack_links_kernel<R12c><<<grid, kBlock, 0, s>>>(lat->geom, R12c{(const float *)internal}, lex_links);
-    else
+    else if (prec == QEX_F32_R12H)
         unpack_links_kernel<R12Hc><<<grid, kBlock, 0, s>>>(lat->geom, R12Hc{(const float *)internal}, lex_links);
+    else
+        unpack_links_kernel<S16c><<<grid, kBlock, 0, s>>>(lat->geom, S16c{(const float *)internal}, lex_links);
     QEX_CHECK_LAUNCH("unpack_links_kernel");
     return QEX_OK;
 }
@@ -351,8 +402,10 @@ qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *
         convert_links_to<const float *>(to, vh, (const float *)in, out, grid, s);
     else if (from == QEX_F32_R12)
         convert_links_to<R12c>(to, vh, R12c{(const float *)in}, out, grid, s);
-    else
+    else if (from == QEX_F32_R12H)
         convert_links_to<R12Hc>(to, vh, R12Hc{(const float *)in}, out, grid, s);
+    else
+        convert_links_to<S16c>(to, vh, S16c{(const float *)in}, out, grid, s);
     QEX_CHECK_LAUNCH("convert_links_kernel");
     return QEX_OK;
 }

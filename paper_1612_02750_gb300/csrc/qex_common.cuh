@@ -243,6 +243,28 @@ __device__ __forceinline__ Mat3<float> load_link_fix16(const float *base_f, size
     return m;
 }
 
+// Full 3x3 links in 16-bit fixed point with a per-link step (for links that
+// are not unitary, e.g. the Naik long links): block (p, mu) holds two planes
+// of 16-byte words (elements 0..3 and 4..7, one offset-binary re/im word per
+// element as above) and a plane of 8-byte words (element 8, then the FP32
+// step d); block size 40*Vh bytes.  Value = q * d.  Returns the integers q in
+// m and the step in *d (the caller folds d into the hop's sign factor).
+__device__ __forceinline__ Mat3<float> load_link_s16(const float *base_f, size_t vh, int p, int mu, int i, float *d) {
+    const char *blk = reinterpret_cast<const char *>(base_f) + (size_t)(p * 4 + mu) * 40 * vh;
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(blk) + i);
+    const uint4 b = __ldg(reinterpret_cast<const uint4 *>(blk + 16 * vh) + i);
+    const uint2 c = __ldg(reinterpret_cast<const uint2 *>(blk + 32 * vh) + i);
+    const uint32_t w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x};
+    Mat3<float> m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        m.e[k].re = fix16_lo(w[k]);
+        m.e[k].im = fix16_hi(w[k]);
+    }
+    *d = __uint_as_float(c.y);
+    return m;
+}
+
 __device__ __forceinline__ Vec3<double> load_vec(const double *base, size_t vh, int i) {
     const double2 *b = reinterpret_cast<const double2 *>(base) + i;
     Vec3<double> v;
@@ -433,8 +455,8 @@ struct qex_lattice {
     void *batch_ctx;           // scratch of qex_cg_batch calls led by this lattice
     cudaEvent_t ev0, ev1;
     // autotuner state (tune.cu): per precision and Naik, and the BLAS grid
-    qex::LaunchShape shape[4][2];
-    int tuned[4][2];           // 0 no, 1 measured, 2 from the cache, 3 defaults (QEX_TUNE=0)
+    qex::LaunchShape shape[5][2];  // [qex_prec][Naik]
+    int tuned[5][2];           // 0 no, 1 measured, 2 from the cache, 3 defaults (QEX_TUNE=0)
     int blas_per_sm;           // 0: QEX_BLAS_BLOCKS_PER_SM
 };
 

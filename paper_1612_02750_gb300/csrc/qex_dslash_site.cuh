@@ -8,7 +8,9 @@ namespace qex {
 
 // Fat-link formats: 0 = full 3x3 in the field precision, 1 = FP32 two-row,
 // 2 = 16-bit fixed-point two-row (third row rebuilt in registers, the matrix
-// held scaled: see load_link_fix16).
+// held scaled: see load_link_fix16), 3 = 16-bit fixed-point full 3x3 with a
+// per-link step (load_link_s16).  Long links are full 3x3 in the field
+// precision for formats 0 and 1, and 16-bit with a per-link step for 2 and 3.
 template <typename R, int FMT>
 __device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int mu, int i) {
     if constexpr (FMT == 1)
@@ -35,31 +37,55 @@ __device__ __forceinline__ Vec3<R> dslash_site(const Geom &g, const R *fat, cons
         const R eta = eta_bit(s, mu) ? R(-1) : R(1);
         {   // + eta b U_mu(x) in(x + mu)
             const int j = hop_index(g, s, mu, 1);
-            const Mat3<R> u = load_fat<R, FMT>(fat, vh, p, mu, i);
-            if constexpr (FMT == 2)
-                acc_mv_fix16(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
-            else
-                acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
+            if constexpr (FMT == 3) {
+                float d;
+                const Mat3<R> u = load_link_s16(fat, vh, p, mu, i, &d);
+                acc_mv(acc, (bc_bit_fwd(g, s, mu, 1) ? -eta : eta) * d, u, in(j));
+            } else {
+                const Mat3<R> u = load_fat<R, FMT>(fat, vh, p, mu, i);
+                if constexpr (FMT == 2)
+                    acc_mv_fix16(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
+                else
+                    acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
+            }
         }
         {   // - eta b U_mu(x - mu)^+ in(x - mu)
             const int j = hop_index(g, s, mu, -1);
-            const Mat3<R> u = load_fat<R, FMT>(fat, vh, 1 - p, mu, j);
-            if constexpr (FMT == 2)
-                acc_mdv_fix16(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
-            else
-                acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
+            if constexpr (FMT == 3) {
+                float d;
+                const Mat3<R> u = load_link_s16(fat, vh, 1 - p, mu, j, &d);
+                acc_mdv(acc, (bc_bit_bwd(g, s, mu, 1) ? eta : -eta) * d, u, in(j));
+            } else {
+                const Mat3<R> u = load_fat<R, FMT>(fat, vh, 1 - p, mu, j);
+                if constexpr (FMT == 2)
+                    acc_mdv_fix16(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
+                else
+                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
+            }
         }
         if (NAIK) {
             const R e3 = c3 * eta;
             {
                 const int j = hop_index(g, s, mu, 3);
-                const Mat3<R> u = load_link(lng, vh, p, mu, i);
-                acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, in(j));
+                if constexpr (FMT >= 2) {
+                    float d;
+                    const Mat3<R> u = load_link_s16(lng, vh, p, mu, i, &d);
+                    acc_mv(acc, (bc_bit_fwd(g, s, mu, 3) ? -e3 : e3) * d, u, in(j));
+                } else {
+                    const Mat3<R> u = load_link(lng, vh, p, mu, i);
+                    acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, in(j));
+                }
             }
             {
                 const int j = hop_index(g, s, mu, -3);
-                const Mat3<R> u = load_link(lng, vh, 1 - p, mu, j);
-                acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, in(j));
+                if constexpr (FMT >= 2) {
+                    float d;
+                    const Mat3<R> u = load_link_s16(lng, vh, 1 - p, mu, j, &d);
+                    acc_mdv(acc, (bc_bit_bwd(g, s, mu, 3) ? e3 : -e3) * d, u, in(j));
+                } else {
+                    const Mat3<R> u = load_link(lng, vh, 1 - p, mu, j);
+                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, in(j));
+                }
             }
         }
     }

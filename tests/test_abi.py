@@ -117,5 +117,9 @@ def test_argument_errors(lib):
     assert lib.qex_links_bytes(h, 2) == 4 * 128 * 12 * 4
     assert lib.qex_field_bytes(h, 2) == 64 * 6 * 4
     assert lib.qex_links_bytes(h, 3) == 4 * 128 * 12 * 2
-    assert lib.qex_pack_links(h, 4, None, None, None) == 1  # unknown precision
+    assert lib.qex_links_bytes(h, 4) == 4 * 128 * 40  # 18 16-bit reals + an FP32 step per link
+    assert lib.qex_field_bytes(h, 4) == 64 * 6 * 4
+    assert lib.qex_pack_links(h, 5, None, None, None) == 1  # unknown precision
+    # long-link format per operator precision: two-row storage never applies to long links
+    assert [lib.qex_long_links_prec(p) for p in range(6)] == [0, 1, 1, 4, 4, -1]
     lib.qex_lattice_destroy(h)

@@ -50,7 +50,7 @@ def _problem(q, dims, mass, seed, naik, inner, zero=False):
             "b64": q.qex_pack_field(lat, "f64", 0, dev(b))}
     if inner != "f64":
         item["fat32"] = q.qex_convert_links(lat, "f64", fat64, inner)
-        item["lng32"] = q.qex_convert_links(lat, "f64", lng64, "f32") if naik else None
+        item["lng32"] = q.qex_convert_links(lat, "f64", lng64, q.qex_long_links_prec(inner)) if naik else None
     import torch
 
     item["x64"] = torch.zeros_like(item["b64"])

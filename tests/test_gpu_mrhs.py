@@ -9,7 +9,7 @@ import fieldgen as fg
 pytestmark = pytest.mark.gpu
 
 C3 = -1.0 / 24.0
-TOL = {"f64": 1e-14, "f32": 1e-6, "f32r12": 1e-6, "f32r12h": 1e-6}
+TOL = {"f64": 1e-14, "f32": 1e-6, "f32r12": 1e-6, "f32r12h": 1e-6, "f32s16": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +37,7 @@ def relerr(a, b):
 
 
 @pytest.mark.parametrize("nrhs", [1, 3, 5, 16, 37])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12", "f32r12h"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12", "f32r12h", "f32s16"])
 @pytest.mark.parametrize("naik", [False, True])
 def test_dslash_mrhs_matches_single(q, nrhs, prec, naik):
     """Each output field of the batched operator equals the single-RHS
@@ -54,7 +54,7 @@ def test_dslash_mrhs_matches_single(q, nrhs, prec, naik):
     lng = None
     if naik:
         w = fg.random_links(dims, "gauss3", s["long_links"])
-        lng = q.qex_pack_links(lat, "f64" if prec == "f64" else "f32", dev(w))
+        lng = q.qex_pack_links(lat, q.qex_long_links_prec(prec), dev(w))
     n = q.qex_field_bytes(lat, prec) // (8 if prec == "f64" else 4)
     for out_p in (0, 1):
         inp = q.empty_fields(lat, prec, nrhs).normal_()

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 C3 = -1.0 / 24.0
 # 16-bit fixed-point links: 1.5e-5 quantisation per real, ~3e-5 per entry of O(0.5)
-TOL = {"f64": 1e-13, "f32": 1e-5, "f32r12": 1e-5, "f32r12h": 1e-4}
+TOL = {"f64": 1e-13, "f32": 1e-5, "f32r12": 1e-5, "f32r12h": 1e-4, "f32s16": 1e-4}
+PRECS = ["f64", "f32", "f32r12", "f32r12h", "f32s16"]
 
 
 @pytest.fixture(scope="module")
@@ -63,12 +64,14 @@ class Setup:
         if fat in ("haar", "exp", "unit"):  # SU(3) links: two-row storage applies
             self.fat["f32r12"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32r12")
             self.fat["f32r12h"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32r12h")
-        self.lng = {"f64": None, "f32": None, "f32r12": None, "f32r12h": None}
+        self.fat["f32s16"] = q.qex_convert_links(self.lat, "f64", self.fat["f64"], "f32s16")
+        self.lng = {p: None for p in PRECS}
         if naik:
             self.lng["f64"] = q.qex_pack_links(self.lat, "f64", dev(self.w))
             self.lng["f32"] = q.qex_pack_links(self.lat, "f32", dev(self.w))
-            self.lng["f32r12"] = self.lng["f32"]  # long links are never compressed
-            self.lng["f32r12h"] = self.lng["f32"]
+            self.lng["f32s16"] = q.qex_pack_links(self.lat, "f32s16", dev(self.w))
+            for p in ("f32r12", "f32r12h"):  # long links are not unitary: never two-row
+                self.lng[p] = self.lng[q.qex_long_links_prec(p)]
 
     def half(self, prec, parity, field):
         return self.q.qex_pack_field(self.lat, prec, parity, dev(field))
@@ -155,9 +158,33 @@ def test_fix16_links_roundtrip(q):
     assert (words & 0xFFFF).min() >= 1 and (words >> 16).min() >= 1  # offset binary: q + 32768, q >= -32767
 
 
+def test_scaled16_links_roundtrip(q):
+    """16-bit links with a per-link step (any links, here non-unitary Gaussian
+    ones): d = max |re|, |im| over the link / 32767 rounded up to FP32, q =
+    round(v * (1/d)); unpack gives q * d; pack and convert agree."""
+    dims = (6, 4, 4, 10)
+    w = fg.random_links(dims, "gauss3", fg.rng_streams(11)["long_links"])
+    w[0, 0, 0, 0, 2] = 0  # a zero link stays zero
+    lat = q.Lattice(dims)
+    h = q.qex_pack_links(lat, "f32s16", dev(w))
+    assert h.numel() * 4 == q.qex_links_bytes(lat, "f32s16") == int(np.prod(dims)) * 4 * 40
+    back = host(q.qex_unpack_links(lat, "f32s16", h))
+    s = np.maximum(np.abs(w.real), np.abs(w.imag)).max(axis=(-2, -1), keepdims=True)
+    d = (s / 32767).astype(np.float32)
+    d = np.where(d.astype(np.float64) < s / 32767, np.nextafter(d, np.float32(np.inf)), d).astype(np.float64)
+    inv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    quant = (np.round(w.real * inv) + 1j * np.round(w.imag * inv)) * d
+    assert np.array_equal(back, quant)
+    assert not back[0, 0, 0, 0, 2].any()
+    err = back - w
+    assert (np.abs(err.real) <= d / 2 * (1 + 1e-12)).all() and (np.abs(err.imag) <= d / 2 * (1 + 1e-12)).all()
+    via = q.qex_convert_links(lat, "f64", q.qex_pack_links(lat, "f64", dev(w)), "f32s16")
+    assert np.array_equal(host(via).view(np.uint32), host(h).view(np.uint32))
+
+
 @pytest.mark.parametrize("dims", SHAPES)
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12", "f32r12h"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_dslash_parity(q, oracle_mod, dims, naik, prec):
     S = Setup(q, dims, naik, seed=21)
     for ap in (True, False):
@@ -183,7 +210,7 @@ def test_dslash_exp_links_and_unit_links(q, oracle_mod):
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f32r12", "f32r12h"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_normal_op_parity(q, oracle_mod, naik, prec):
     dims = (8, 4, 6, 10)
     S = Setup(q, dims, naik, seed=22)
@@ -221,14 +248,15 @@ def _cg(q, S, inner, m, b_full, tol=1e-10, maxiter=20000, delta=0.1, x0=None):
 
     b = S.half("f64", 0, b_full)
     x = S.half("f64", 0, x0) if x0 is not None else torch.zeros_like(b)
-    f32 = inner if inner in ("f32r12", "f32r12h") else "f32"
-    st, stats = q.qex_cg(S.lat, inner, S.fat["f64"], S.lng["f64"], S.fat[f32], S.lng["f32"], C3, m, b, x,
+    inner_fat = S.fat[inner if inner != "f64" else "f32"]
+    inner_lng = S.lng[q.qex_long_links_prec(inner) if inner != "f64" else "f32"]
+    st, stats = q.qex_cg(S.lat, inner, S.fat["f64"], S.lng["f64"], inner_fat, inner_lng, C3, m, b, x,
                          tol=tol, maxiter=maxiter, delta=delta, check=False)
     return st, stats, S.full("f64", 0, x)
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("inner", ["f64", "f32", "f32r12", "f32r12h"])
+@pytest.mark.parametrize("inner", PRECS)
 def test_cg_parity(q, oracle_mod, naik, inner):
     dims = (8, 8, 4, 8)
     m = 0.1

@@ -38,7 +38,7 @@ def dev(a):
 
 
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 4, 10), (16, 16, 16, 16)])
-@pytest.mark.parametrize("prec", ["f64", "f32r12h"])
+@pytest.mark.parametrize("prec", ["f64", "f32r12h", "f32s16"])
 @pytest.mark.parametrize("naik", [False, True])
 def test_tuned_shapes_keep_dslash_bits(q, monkeypatch, dims, prec, naik):
     """The plain and normal-operator Dslash give bit-identical fields with the
@@ -54,7 +54,7 @@ def test_tuned_shapes_keep_dslash_bits(q, monkeypatch, dims, prec, naik):
     lng = None
     if naik:
         w = fg.random_links(dims, "gauss3", s["long_links"])
-        lng = q.qex_pack_links(lat, "f64" if prec == "f64" else "f32", dev(w))
+        lng = q.qex_pack_links(lat, q.qex_long_links_prec(prec), dev(w))
     inp = q.empty_field(lat, prec).normal_()
     monkeypatch.setenv("QEX_TUNE", "0")
     ref = q.qex_dslash(lat, prec, fat, lng, C3, 1, inp)
