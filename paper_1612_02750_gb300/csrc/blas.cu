@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(kBlock)
 update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf1, const R *__restrict__ ap,
                  CgScalars *S, double *partials, unsigned int *counter, const GraphCtl ctl) {
     __shared__ double smem[32];
+    pdl_trigger();
+    pdl_wait();
     if (S->halt) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_conditions(ctl, 0u, 0u);
         return;
@@ -112,6 +114,8 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf
 template <typename R>
 __global__ void __launch_bounds__(kBlock)
 update_p_kernel(int vh, const R *__restrict__ r, R *pbuf0, R *pbuf1, const CgScalars *S) {
+    pdl_trigger();
+    pdl_wait();
     if (S->halt) return;
     const int it = S->iters;
     const R *pold = (it & 1) ? pbuf1 : pbuf0;
@@ -131,6 +135,8 @@ update_p_kernel(int vh, const R *__restrict__ r, R *pbuf0, R *pbuf1, const CgSca
 
 // x64 += xh32; xh32 = 0
 __global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restrict__ x, float *__restrict__ xh) {
+    pdl_trigger();
+    pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
         Vec3<double> xv = load_vec(x, vh, i);
         const Vec3<float> hv = load_vec(xh, vh, i);
@@ -152,6 +158,8 @@ __global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restr
 __global__ void __launch_bounds__(kBlock)
 finish_ru_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32, const CgScalars *S,
                  const GraphCtl ctl) {
+    pdl_trigger();
+    pdl_wait();
     if (r32) {
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
             const Vec3<double> rd = load_vec(r64, vh, i);
@@ -169,6 +177,8 @@ finish_ru_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32
 }
 
 __global__ void __launch_bounds__(kBlock) any_nonzero_kernel(size_t n2, const double2 *__restrict__ f, int *flag) {
+    pdl_trigger();
+    pdl_wait();
     int nz = 0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
         const double2 v = __ldg(f + i);
@@ -181,6 +191,8 @@ template <typename R>
 __global__ void __launch_bounds__(kBlock)
 norm2_kernel(int vh, const R *__restrict__ f, double *out, CgScalars *S, double *partials, unsigned int *counter) {
     __shared__ double smem[32];
+    pdl_trigger();
+    pdl_wait();
     double part = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x)
         part += (double)norm2_site(load_vec(f, vh, i));
@@ -242,13 +254,11 @@ qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, v
                             CgScalars *S, const GraphCtl &ctl, cudaStream_t st) {
     int nb = blas_blocks(lat), vh = (int)lat->vh;
     if (prec == QEX_F64)
-        update_xr_kernel<double><<<nb, kBlock, 0, st>>>(vh, (double *)x, (double *)r, (double *)pbuf[0],
-                                                        (double *)pbuf[1], (const double *)ap, S, lat->partials,
-                                                        lat->counter, ctl);
+        launch_k(update_xr_kernel<double>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (double *)x, (double *)r,
+                 (double *)pbuf[0], (double *)pbuf[1], (const double *)ap, S, lat->partials, lat->counter, ctl);
     else
-        update_xr_kernel<float><<<nb, kBlock, 0, st>>>(vh, (float *)x, (float *)r, (float *)pbuf[0],
-                                                       (float *)pbuf[1], (const float *)ap, S, lat->partials,
-                                                       lat->counter, ctl);
+        launch_k(update_xr_kernel<float>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (float *)x, (float *)r,
+                 (float *)pbuf[0], (float *)pbuf[1], (const float *)ap, S, lat->partials, lat->counter, ctl);
     QEX_CHECK_LAUNCH("update_xr_kernel");
     return QEX_OK;
 }
@@ -257,22 +267,25 @@ qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void 
                            cudaStream_t st) {
     int nb = blas_blocks(lat), vh = (int)lat->vh;
     if (prec == QEX_F64)
-        update_p_kernel<double><<<nb, kBlock, 0, st>>>(vh, (const double *)r, (double *)pbuf[0], (double *)pbuf[1], S);
+        launch_k(update_p_kernel<double>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (const double *)r,
+                 (double *)pbuf[0], (double *)pbuf[1], (const CgScalars *)S);
     else
-        update_p_kernel<float><<<nb, kBlock, 0, st>>>(vh, (const float *)r, (float *)pbuf[0], (float *)pbuf[1], S);
+        launch_k(update_p_kernel<float>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (const float *)r,
+                 (float *)pbuf[0], (float *)pbuf[1], (const CgScalars *)S);
     QEX_CHECK_LAUNCH("update_p_kernel");
     return QEX_OK;
 }
 
 qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st) {
-    accum_x_kernel<<<blas_blocks(lat), kBlock, 0, st>>>((int)lat->vh, x64, xh32);
+    launch_k(accum_x_kernel, dim3(blas_blocks(lat)), dim3(kBlock), 0, st, lat->pdl != 0, (int)lat->vh, x64, xh32);
     QEX_CHECK_LAUNCH("accum_x_kernel");
     return QEX_OK;
 }
 
 qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, const CgScalars *S,
                             const GraphCtl &ctl, cudaStream_t st) {
-    finish_ru_kernel<<<r32 ? blas_blocks(lat) : 1, kBlock, 0, st>>>((int)lat->vh, r64, r32, S, ctl);
+    launch_k(finish_ru_kernel, dim3(r32 ? blas_blocks(lat) : 1), dim3(kBlock), 0, st, lat->pdl != 0, (int)lat->vh, r64,
+             r32, S, ctl);
     QEX_CHECK_LAUNCH("finish_ru_kernel");
     return QEX_OK;
 }

@@ -41,6 +41,8 @@ template <typename R, int FMT, bool NAIK, int EPI>
 __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslash_kernel(const DsParams<R> P) {
     __shared__ double smem[32];
     __shared__ unsigned int is_last;
+    pdl_trigger();
+    pdl_wait();  // everything below may read what earlier kernels wrote
     if (P.check_halt && P.S->halt) return;  // uniform over the grid
     // first residual from a zero initial guess: D x = 0 (uniform over the grid)
     const bool zero_x = P.skip_zero_x && !P.S->x_nonzero;
@@ -213,7 +215,7 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     int grid, block;
     dslash_shape(lat, a.prec, NAIK, EPI != EPI_PLAIN && EPI != EPI_PUPD && a.S != nullptr, DslashMinBlocks<R>::value,
                  &grid, &block);
-    dslash_kernel<R, FMT, NAIK, EPI><<<grid, block, 0, st>>>(P);
+    launch_k(dslash_kernel<R, FMT, NAIK, EPI>, dim3(grid), dim3(block), 0, st, lat->pdl != 0, P);
 }
 
 template <typename R, int FMT, bool NAIK>

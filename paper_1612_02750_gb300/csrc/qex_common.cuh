@@ -4,6 +4,8 @@
 // reductions and the error plumbing of the C ABI.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -419,6 +421,31 @@ __device__ __forceinline__ double block_sum_partials(const double *partial, int 
     return block_sum(s, smem);
 }
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel launched with the programmatic-serialization attribute may start
+// while its predecessor in the stream is still finishing: each kernel of the
+// CG path lets the next one launch at once (pdl_trigger) and waits for its
+// predecessors' completion and memory (pdl_wait) before it reads anything;
+// for an ordinary launch both return at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                     Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ------------------------------------------------------- lattice object
 struct CgScalars;
 
@@ -458,6 +485,7 @@ struct qex_lattice {
     qex::LaunchShape shape[5][2];  // [qex_prec][Naik]
     int tuned[5][2];           // 0 no, 1 measured, 2 from the cache, 3 defaults (QEX_TUNE=0)
     int blas_per_sm;           // 0: QEX_BLAS_BLOCKS_PER_SM
+    int pdl;                   // CG kernels launch with programmatic dependent launch (set by qex_cg)
 };
 
 namespace qex {
