@@ -361,9 +361,10 @@ qex_status qex_cg_host(const qex_lattice *lat, qex_prec inner, const double *hos
  * synchronises the stream.  Errors: QEX_ERR_ARG (null fat, or the stream is
  * being captured), QEX_ERR_ALIGN, QEX_ERR_SHAPE (Naik with an extent < 4),
  * QEX_ERR_CUDA.
- * qex_dslash, qex_normal_op and qex_cg tune on their first uncaptured call
- * for a (prec, Naik) unless QEX_TUNE=0, taking the cache (file included) when
- * it holds the key.  Per-site results do not depend on the shape; FP64 sums
+ * qex_dslash, qex_normal_op and qex_cg tune the Dslash shapes (not the
+ * vector-update grid, which only qex_tune measures) on their first uncaptured
+ * call for a (prec, Naik) unless QEX_TUNE=0, taking the cache (file included)
+ * when it holds the key.  Per-site results do not depend on the shape; FP64 sums
  * over blocks (CG reductions) are bit-reproducible for a given shape. */
 qex_status qex_tune(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng, void *stream);
 

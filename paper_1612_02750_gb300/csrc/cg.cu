@@ -320,9 +320,11 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     s.b64 = (const double *)b64;
     s.x64 = (double *)x64;
     const cudaStream_t cst = as_stream(stream);
-    // launch shapes of the inner iteration (with the vector update's grid)
-    // and of the FP64 reliable updates, before the graph bakes them in
-    if ((st = ensure_tuned(lat, inner, mixed ? fat32 : fat64, mixed ? lng32 : lng64, cst, true))) return st;
+    // launch shapes of the inner iteration and of the FP64 reliable updates,
+    // before the graph bakes them in (the vector kernels keep their compiled
+    // grid: timed alone on L2-resident scratch they favour grids that are
+    // slower inside the solve)
+    if ((st = ensure_tuned(lat, inner, mixed ? fat32 : fat64, mixed ? lng32 : lng64, cst, false))) return st;
     if (mixed && (st = ensure_tuned(lat, QEX_F64, fat64, lng64, cst, false))) return st;
     if ((st = carve(lat, mixed, s.B))) return st;
     // programmatic dependent launch: on for the host-driven loop (measured

@@ -12,15 +12,20 @@
 
 namespace qex {
 
-// Thread mapping: lane = 4 * site_in_warp + k, one right-hand side per
-// thread; the four lanes of a site load the same link words (one broadcast
-// transaction) and their own vectors.  A block is 8 warps = 64 sites x 4
-// right-hand sides; linear block b covers site block b / ngroups and
-// right-hand-side group b % ngroups, so the blocks that reuse a link run
-// back to back and find it in L2.
-constexpr int kMrhsGroup = 4;                  // right-hand sides per site within a warp
-constexpr int kMrhsBlock = 256;                // threads per block
-constexpr int kMrhsSitesPerBlock = kMrhsBlock / kMrhsGroup;
+// Thread mapping: one output site per thread and a group of KR right-hand
+// sides per thread (KR = 4 in FP32, 2 in FP64, held in registers): each
+// link is loaded and decoded once per group and applied to all KR vectors.
+// A block is 256 sites of one group; linear block b covers site block
+// b / ngroups and group b % ngroups, so the blocks that reuse a link run back
+// to back and find it in L2.
+constexpr int kMrhsBlock = 256;  // threads (sites) per block
+// Resident blocks per SM (the register cap: 128 per thread leaves the KR
+// accumulators, the KR input vectors of a hop and a decoded link in registers;
+// the KR independent mat-vecs supply the instruction-level parallelism that
+// the lower occupancy gives up).
+constexpr int kMrhsMinBlocks = 2;
+template <typename R> struct MrhsPerThread { static constexpr int value = 4; };
+template <> struct MrhsPerThread<double> { static constexpr int value = 2; };
 
 template <typename R>
 struct MParams {
@@ -42,8 +47,9 @@ struct MParams {
 };
 
 template <typename R, int FMT, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParams<R> P) {
-    __shared__ double wsum[kMrhsBlock / 32][kMrhsGroup];
+__global__ void __launch_bounds__(kMrhsBlock, kMrhsMinBlocks) dslash_mrhs_kernel(const MParams<R> P) {
+    constexpr int KR = MrhsPerThread<R>::value;
+    __shared__ double wsum[kMrhsBlock / 32][KR];
     __shared__ unsigned int is_last;
     MrhsScalars *S = P.S;
     if (P.check_halt && S->halt) return;  // uniform over the grid
@@ -51,9 +57,7 @@ __global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParam
     const size_t vh = (size_t)g.vh;
     const size_t fstride = 6 * vh;  // reals per half field
     const int p = P.p;
-    const int k = threadIdx.x & (kMrhsGroup - 1);
-    const int sub = threadIdx.x / kMrhsGroup;
-    const int nsb = (int)((vh + kMrhsSitesPerBlock - 1) / kMrhsSitesPerBlock);
+    const int nsb = (int)((vh + kMrhsBlock - 1) / kMrhsBlock);
     const int total = nsb * P.ngroups;
     const R *pold = nullptr;
     R *pnew = nullptr;
@@ -62,74 +66,97 @@ __global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParam
         pold = (it & 1) ? P.pbuf1 : P.pbuf0;
         pnew = (it & 1) ? P.pbuf0 : P.pbuf1;
     }
-    double part = 0.0;
+    double part[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) part[k] = 0.0;
     // reducing launches have gridDim.x a multiple of ngroups: the group is fixed per block
     for (int bl = blockIdx.x; bl < total; bl += gridDim.x) {
         const int grp = bl % P.ngroups;
-        const int rh = grp * kMrhsGroup + k;
-        const int i = (bl / P.ngroups) * kMrhsSitesPerBlock + sub;
-        const bool act = i < g.vh && rh < P.nrhs && (S == nullptr || S->active[rh]);
-        if (!act) continue;
-        const R beta = (EPI == EPI_PUPD) ? (R)S->beta[rh] : R(0);
-        const size_t off = (size_t)rh * fstride;
+        const int i = (bl / P.ngroups) * kMrhsBlock + threadIdx.x;
+        if (i >= g.vh) continue;
+        bool act[KR];
+        R beta[KR];
+        size_t off[KR];
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int rh = grp * KR + k;  // uniform over the block
+            act[k] = rh < P.nrhs && (S == nullptr || S->active[rh]);
+            any |= act[k];
+            off[k] = (size_t)(act[k] ? rh : 0) * fstride;
+            beta[k] = (EPI == EPI_PUPD && act[k]) ? (R)S->beta[rh] : R(0);
+        }
+        if (!any) continue;
         const Site s = site_of(g, p, i);
-        const R *rin = (EPI == EPI_PUPD) ? P.r + off : P.in + off;
-        const R *pin = (EPI == EPI_PUPD) ? pold + off : nullptr;
-        const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, P.fat, P.lng, P.c3, p, i, s, [&](int j) {
-            if constexpr (EPI == EPI_PUPD)
-                return axpy_vec(rin, pin, beta, vh, j);
-            else
-                return load_vec(rin, vh, j);
-        });
-        if constexpr (EPI == EPI_PLAIN) {
-            store_vec(P.out + off, vh, i, acc);
-        } else if constexpr (EPI == EPI_PUPD) {
-            store_vec(P.out + off, vh, i, acc);
-            store_vec(pnew + off, vh, i, axpy_vec(rin, pin, beta, vh, i));
-        } else if constexpr (EPI == EPI_NORMAL) {
-            const Vec3<R> qv = load_vec(pnew + off, vh, i);
-            Vec3<R> o;
-            R d = R(0);
+        Vec3<R> acc[KR];
+        dslash_site_n<R, FMT, NAIK, KR>(g, P.fat, P.lng, P.c3, p, i, s, [&](int j, int k) {
+            Vec3<R> v;
+            if (!act[k]) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                o.c[a].re = fma(P.m2, qv.c[a].re, -acc.c[a].re);
-                o.c[a].im = fma(P.m2, qv.c[a].im, -acc.c[a].im);
-                d = fma(qv.c[a].re, o.c[a].re, d);
-                d = fma(qv.c[a].im, o.c[a].im, d);
+                for (int a = 0; a < 3; ++a) v.c[a].re = v.c[a].im = R(0);
+            } else if constexpr (EPI == EPI_PUPD) {
+                v = axpy_vec(P.r + off[k], pold + off[k], beta[k], vh, j);
+            } else {
+                v = load_vec(P.in + off[k], vh, j);
             }
-            store_vec(P.out + off, vh, i, o);
-            part += (double)d;
-        } else {  // EPI_RESID, FP64: out = b - m^2 x + D in
-            const Vec3<R> qv = load_vec(P.q + off, vh, i);
-            const Vec3<double> bv = load_vec(P.b + off, vh, i);
-            Vec3<R> o;
-            double d = 0.0;
+            return v;
+        }, acc);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                o.c[a].re = (R)bv.c[a].re - fma(P.m2, qv.c[a].re, -acc.c[a].re);
-                o.c[a].im = (R)bv.c[a].im - fma(P.m2, qv.c[a].im, -acc.c[a].im);
-                d = fma((double)o.c[a].re, (double)o.c[a].re, d);
-                d = fma((double)o.c[a].im, (double)o.c[a].im, d);
+        for (int k = 0; k < KR; ++k) {
+            if (!act[k]) continue;
+            if constexpr (EPI == EPI_PLAIN) {
+                store_vec(P.out + off[k], vh, i, acc[k]);
+            } else if constexpr (EPI == EPI_PUPD) {
+                store_vec(P.out + off[k], vh, i, acc[k]);
+                store_vec(pnew + off[k], vh, i, axpy_vec(P.r + off[k], pold + off[k], beta[k], vh, i));
+            } else if constexpr (EPI == EPI_NORMAL) {
+                const Vec3<R> qv = load_vec(pnew + off[k], vh, i);
+                Vec3<R> o;
+                R d = R(0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    o.c[a].re = fma(P.m2, qv.c[a].re, -acc[k].c[a].re);
+                    o.c[a].im = fma(P.m2, qv.c[a].im, -acc[k].c[a].im);
+                    d = fma(qv.c[a].re, o.c[a].re, d);
+                    d = fma(qv.c[a].im, o.c[a].im, d);
+                }
+                store_vec(P.out + off[k], vh, i, o);
+                part[k] += (double)d;
+            } else {  // EPI_RESID, FP64: out = b - m^2 x + D in
+                const Vec3<R> qv = load_vec(P.q + off[k], vh, i);
+                const Vec3<double> bv = load_vec(P.b + off[k], vh, i);
+                Vec3<R> o;
+                double d = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    o.c[a].re = (R)bv.c[a].re - fma(P.m2, qv.c[a].re, -acc[k].c[a].re);
+                    o.c[a].im = (R)bv.c[a].im - fma(P.m2, qv.c[a].im, -acc[k].c[a].im);
+                    d = fma((double)o.c[a].re, (double)o.c[a].re, d);
+                    d = fma((double)o.c[a].im, (double)o.c[a].im, d);
+                }
+                store_vec(P.out + off[k], vh, i, o);
+                part[k] += d;
             }
-            store_vec(P.out + off, vh, i, o);
-            part += d;
         }
     }
     if constexpr (EPI == EPI_PLAIN || EPI == EPI_PUPD) {
         return;
     } else {
-        // per right-hand side of this block's group: lanes with equal k sum
-        // within the warp, then warps in order -> partials[blockIdx.x][k]
-        double v = part;
-#pragma unroll
-        for (int o = 16; o >= kMrhsGroup; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        // per right-hand side of this block's group: a fixed shuffle tree in
+        // each warp, then warps in order -> partials[blockIdx.x * KR + k]
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane < kMrhsGroup) wsum[warp][lane] = v;
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            double v = part[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) wsum[warp][k] = v;
+        }
         __syncthreads();
-        if (threadIdx.x < kMrhsGroup) {
+        if (threadIdx.x < KR) {
             double t = 0.0;
             for (int w = 0; w < kMrhsBlock / 32; ++w) t += wsum[w][threadIdx.x];
-            P.partials[(size_t)blockIdx.x * kMrhsGroup + threadIdx.x] = t;
+            P.partials[(size_t)blockIdx.x * KR + threadIdx.x] = t;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -140,13 +167,13 @@ __global__ void __launch_bounds__(kMrhsBlock, 3) dslash_mrhs_kernel(const MParam
         __syncthreads();
         if (!is_last) return;
         __threadfence();
-        // right-hand side r = grp * 4 + k lives in blocks bx = grp (mod ngroups)
+        // right-hand side r = grp * KR + k lives in blocks bx = grp (mod ngroups)
         const int nw = kMrhsBlock / 32;
         for (int r = warp; r < P.nrhs; r += nw) {
-            const int grp = r / kMrhsGroup, kk = r % kMrhsGroup;
+            const int grp = r / KR, kk = r % KR;
             double t = 0.0;
             for (int bx = grp + lane * P.ngroups; bx < (int)gridDim.x; bx += 32 * P.ngroups)
-                t += __ldcg(P.partials + (size_t)bx * kMrhsGroup + kk);
+                t += __ldcg(P.partials + (size_t)bx * KR + kk);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
             if (lane != 0 || !S->active[r]) continue;
@@ -198,7 +225,8 @@ static void launch_m(const qex_lattice *lat, const MrhsArgs &a, cudaStream_t st)
     P.c3 = (R)a.c3;
     P.p = a.out_parity;
     P.nrhs = a.nrhs;
-    P.ngroups = (a.nrhs + kMrhsGroup - 1) / kMrhsGroup;
+    constexpr int KR = MrhsPerThread<R>::value;
+    P.ngroups = (a.nrhs + KR - 1) / KR;
     P.in = (const R *)a.in;
     P.out = (R *)a.out;
     P.q = (const R *)a.q;
@@ -211,11 +239,11 @@ static void launch_m(const qex_lattice *lat, const MrhsArgs &a, cudaStream_t st)
     P.pbuf1 = (R *)a.pbuf[1];
     P.partials = lat->partials;
     P.counter = lat->counter;
-    const int nsb = (int)((lat->vh + kMrhsSitesPerBlock - 1) / kMrhsSitesPerBlock);
+    const int nsb = (int)((lat->vh + kMrhsBlock - 1) / kMrhsBlock);
     const int total = nsb * P.ngroups;
     int gx = total;
     if (EPI == EPI_NORMAL || EPI == EPI_RESID) {  // persistent grid, a multiple of ngroups
-        int cap = sm_count() * 3;
+        int cap = sm_count() * kMrhsMinBlocks;
         cap -= cap % P.ngroups;
         if (cap < P.ngroups) cap = P.ngroups;
         gx = total < cap ? total : cap;
@@ -239,7 +267,7 @@ qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t 
     if (a.epi == EPI_NORMAL || a.epi == EPI_RESID) {
         qex_status s = ensure_scratch(lat);
         if (s) return s;
-        const size_t need = (size_t)(sm_count() * 3 + 1) * kMrhsGroup;
+        const size_t need = (size_t)(sm_count() * kMrhsMinBlocks + 1) * MrhsPerThread<float>::value;
         if ((size_t)lat->partials_len < need) {
             set_error("internal: partials buffer too small for %d right-hand sides", a.nrhs);
             return QEX_ERR_ARG;

@@ -21,75 +21,101 @@ __device__ __forceinline__ Mat3<R> load_fat(const R *base, size_t vh, int p, int
         return load_link(base, vh, p, mu, i);
 }
 
-// (D in)(x) for the i-th site x (= s) of parity p:
+// (D in_k)(x), k = 0..K-1, for the i-th site x (= s) of parity p:
 //   sum_mu eta b U_mu(x) in(x+mu) - eta b U_mu(x-mu)^+ in(x-mu)
 //   + c3 (the same with the long links and x +- 3mu)           [NAIK]
-// `in(j)` returns the input vector at index j of the other parity.
-template <typename R, int FMT, bool NAIK, typename In>
-__device__ __forceinline__ Vec3<R> dslash_site(const Geom &g, const R *fat, const R *lng, R c3, int p, int i,
-                                               const Site &s, const In &in) {
+// `in(j, k)` returns the input vector of field k at index j of the other
+// parity.  Each link is loaded and decoded once and applied to all K fields.
+template <typename R, int FMT, bool NAIK, int K, typename In>
+__device__ __forceinline__ void dslash_site_n(const Geom &g, const R *fat, const R *lng, R c3, int p, int i,
+                                              const Site &s, const In &in, Vec3<R> (&acc)[K]) {
     const size_t vh = (size_t)g.vh;
-    Vec3<R> acc;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) acc.c[a].re = acc.c[a].im = R(0);
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[k].c[a].re = acc[k].c[a].im = R(0);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         const R eta = eta_bit(s, mu) ? R(-1) : R(1);
         {   // + eta b U_mu(x) in(x + mu)
             const int j = hop_index(g, s, mu, 1);
+            const R sg = bc_bit_fwd(g, s, mu, 1) ? -eta : eta;
             if constexpr (FMT == 3) {
                 float d;
                 const Mat3<R> u = load_link_s16(fat, vh, p, mu, i, &d);
-                acc_mv(acc, (bc_bit_fwd(g, s, mu, 1) ? -eta : eta) * d, u, in(j));
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc_mv(acc[k], sg * d, u, in(j, k));
             } else {
                 const Mat3<R> u = load_fat<R, FMT>(fat, vh, p, mu, i);
-                if constexpr (FMT == 2)
-                    acc_mv_fix16(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
-                else
-                    acc_mv(acc, bc_bit_fwd(g, s, mu, 1) ? -eta : eta, u, in(j));
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if constexpr (FMT == 2)
+                        acc_mv_fix16(acc[k], sg, u, in(j, k));
+                    else
+                        acc_mv(acc[k], sg, u, in(j, k));
+                }
             }
         }
         {   // - eta b U_mu(x - mu)^+ in(x - mu)
             const int j = hop_index(g, s, mu, -1);
+            const R sg = bc_bit_bwd(g, s, mu, 1) ? eta : -eta;
             if constexpr (FMT == 3) {
                 float d;
                 const Mat3<R> u = load_link_s16(fat, vh, 1 - p, mu, j, &d);
-                acc_mdv(acc, (bc_bit_bwd(g, s, mu, 1) ? eta : -eta) * d, u, in(j));
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc_mdv(acc[k], sg * d, u, in(j, k));
             } else {
                 const Mat3<R> u = load_fat<R, FMT>(fat, vh, 1 - p, mu, j);
-                if constexpr (FMT == 2)
-                    acc_mdv_fix16(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
-                else
-                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 1) ? eta : -eta, u, in(j));
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if constexpr (FMT == 2)
+                        acc_mdv_fix16(acc[k], sg, u, in(j, k));
+                    else
+                        acc_mdv(acc[k], sg, u, in(j, k));
+                }
             }
         }
         if (NAIK) {
             const R e3 = c3 * eta;
             {
                 const int j = hop_index(g, s, mu, 3);
+                const R sg = bc_bit_fwd(g, s, mu, 3) ? -e3 : e3;
                 if constexpr (FMT >= 2) {
                     float d;
                     const Mat3<R> u = load_link_s16(lng, vh, p, mu, i, &d);
-                    acc_mv(acc, (bc_bit_fwd(g, s, mu, 3) ? -e3 : e3) * d, u, in(j));
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc_mv(acc[k], sg * d, u, in(j, k));
                 } else {
                     const Mat3<R> u = load_link(lng, vh, p, mu, i);
-                    acc_mv(acc, bc_bit_fwd(g, s, mu, 3) ? -e3 : e3, u, in(j));
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc_mv(acc[k], sg, u, in(j, k));
                 }
             }
             {
                 const int j = hop_index(g, s, mu, -3);
+                const R sg = bc_bit_bwd(g, s, mu, 3) ? e3 : -e3;
                 if constexpr (FMT >= 2) {
                     float d;
                     const Mat3<R> u = load_link_s16(lng, vh, 1 - p, mu, j, &d);
-                    acc_mdv(acc, (bc_bit_bwd(g, s, mu, 3) ? e3 : -e3) * d, u, in(j));
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc_mdv(acc[k], sg * d, u, in(j, k));
                 } else {
                     const Mat3<R> u = load_link(lng, vh, 1 - p, mu, j);
-                    acc_mdv(acc, bc_bit_bwd(g, s, mu, 3) ? e3 : -e3, u, in(j));
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc_mdv(acc[k], sg, u, in(j, k));
                 }
             }
         }
     }
-    return acc;
+}
+
+// One field: (D in)(x), `in(j)` the input vector at index j.
+template <typename R, int FMT, bool NAIK, typename In>
+__device__ __forceinline__ Vec3<R> dslash_site(const Geom &g, const R *fat, const R *lng, R c3, int p, int i,
+                                               const Site &s, const In &in) {
+    Vec3<R> acc[1];
+    dslash_site_n<R, FMT, NAIK, 1>(g, fat, lng, c3, p, i, s, [&](int j, int) { return in(j); }, acc);
+    return acc[0];
 }
 
 // r + beta p at index j (the CG direction formed on the fly).
