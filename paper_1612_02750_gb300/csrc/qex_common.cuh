@@ -325,6 +325,51 @@ __device__ __forceinline__ void acc_mv(Vec3<R> &acc, R sgn, const Mat3<R> &m, co
     }
 }
 
+// FP64 hops whose factor is +1 or -1 (the one-hop term): the sign goes into
+// the input vector as an XOR of its sign bits (integer pipe) and the mat-vec
+// accumulates straight into acc, 36 FP64 FMAs per hop instead of 42.
+__device__ __forceinline__ Vec3<double> flip_sign(const Vec3<double> &v, bool neg) {
+    const unsigned long long m = neg ? 0x8000000000000000ull : 0ull;
+    Vec3<double> w;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w.c[a].re = __longlong_as_double(__double_as_longlong(v.c[a].re) ^ m);
+        w.c[a].im = __longlong_as_double(__double_as_longlong(v.c[a].im) ^ m);
+    }
+    return w;
+}
+
+// acc += (neg ? -1 : 1) * (M v)
+__device__ __forceinline__ void acc_mv_unit(Vec3<double> &acc, bool neg, const Mat3<double> &m, const Vec3<double> &v) {
+    const Vec3<double> w = flip_sign(v, neg);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            acc.c[a].re = fma(m.e[3 * a + b].re, w.c[b].re, acc.c[a].re);
+            acc.c[a].re = fma(-m.e[3 * a + b].im, w.c[b].im, acc.c[a].re);
+            acc.c[a].im = fma(m.e[3 * a + b].re, w.c[b].im, acc.c[a].im);
+            acc.c[a].im = fma(m.e[3 * a + b].im, w.c[b].re, acc.c[a].im);
+        }
+    }
+}
+
+// acc += (neg ? -1 : 1) * (M^+ v)
+__device__ __forceinline__ void acc_mdv_unit(Vec3<double> &acc, bool neg, const Mat3<double> &m,
+                                             const Vec3<double> &v) {
+    const Vec3<double> w = flip_sign(v, neg);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            acc.c[a].re = fma(m.e[3 * b + a].re, w.c[b].re, acc.c[a].re);
+            acc.c[a].re = fma(m.e[3 * b + a].im, w.c[b].im, acc.c[a].re);
+            acc.c[a].im = fma(m.e[3 * b + a].re, w.c[b].im, acc.c[a].im);
+            acc.c[a].im = fma(-m.e[3 * b + a].im, w.c[b].re, acc.c[a].im);
+        }
+    }
+}
+
 // acc += sgn * (U v) for U held as load_link_fix16 returns it.
 __device__ __forceinline__ void acc_mv_fix16(Vec3<float> &acc, float sgn, const Mat3<float> &m, const Vec3<float> &v) {
 #pragma unroll

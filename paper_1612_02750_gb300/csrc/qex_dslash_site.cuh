@@ -2,6 +2,8 @@
 // shared by the single-field, multi-RHS and multi-lattice kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "qex_common.cuh"
 
 namespace qex {
@@ -51,6 +53,8 @@ __device__ __forceinline__ void dslash_site_n(const Geom &g, const R *fat, const
                 for (int k = 0; k < K; ++k) {
                     if constexpr (FMT == 2)
                         acc_mv_fix16(acc[k], sg, u, in(j, k));
+                    else if constexpr (std::is_same<R, double>::value)
+                        acc_mv_unit(acc[k], sg < R(0), u, in(j, k));
                     else
                         acc_mv(acc[k], sg, u, in(j, k));
                 }
@@ -70,6 +74,8 @@ __device__ __forceinline__ void dslash_site_n(const Geom &g, const R *fat, const
                 for (int k = 0; k < K; ++k) {
                     if constexpr (FMT == 2)
                         acc_mdv_fix16(acc[k], sg, u, in(j, k));
+                    else if constexpr (std::is_same<R, double>::value)
+                        acc_mdv_unit(acc[k], sg < R(0), u, in(j, k));
                     else
                         acc_mdv(acc[k], sg, u, in(j, k));
                 }
