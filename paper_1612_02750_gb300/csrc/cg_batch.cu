@@ -104,16 +104,17 @@ __device__ __forceinline__ void set_conds(const GraphCtl &ctl, unsigned int loop
     }
 }
 
-// After the per-tile partials of this launch are written: the last block
-// sums each listed lattice's tiles in order (one warp per lattice) into tot[].
+// After the per-tile partials of this launch are written: the last of the
+// nblocks participating blocks sums each listed lattice's tiles in order
+// (one warp per lattice) into tot[].
 __device__ __forceinline__ bool last_block_totals(double *partials, unsigned int *counter, int nl, const int *start,
-                                                  double *tot) {
+                                                  double *tot, unsigned int nblocks) {
     __shared__ unsigned int is_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int t = atomicAdd(counter, 1u);
-        is_last = (t == gridDim.x - 1) ? 1u : 0u;
+        is_last = (t == nblocks - 1) ? 1u : 0u;
     }
     __syncthreads();
     if (!is_last) return false;
@@ -141,6 +142,10 @@ batch_iter_dslash_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, dou
     const int nl = S->nlist;
     const int ntiles = S->astart[nl];
     const int it = S->iter;
+    // blocks beyond the running tiles leave at once (the last running lattice
+    // can be a few tiles against a grid sized for all of them)
+    const unsigned int nblk = ntiles < (int)gridDim.x ? (unsigned int)ntiles : gridDim.x;
+    if (blockIdx.x >= nblk) return;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int k = find_start(S->astart, nl, t);
         const int l = S->alist[k];
@@ -186,7 +191,7 @@ batch_iter_dslash_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, dou
         }
     }
     if constexpr (ROLE == ROLE_K2) {
-        if (!last_block_totals(partials, counter, nl, S->astart, tot)) return;
+        if (!last_block_totals(partials, counter, nl, S->astart, tot, nblk)) return;
         if (threadIdx.x != 0) return;
         for (int k = 0; k < nl; ++k) {
             const int l = S->alist[k];
@@ -218,6 +223,8 @@ batch_update_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *
     if (blockIdx.x == 0 && threadIdx.x == 0) set_conds(ctl, 0u, 0u);
     const int nl = S->nlist;
     const int ntiles = S->astart[nl];
+    const unsigned int nblk = ntiles < (int)gridDim.x ? (unsigned int)ntiles : gridDim.x;
+    if (blockIdx.x >= nblk) return;  // a running list is never empty here (an empty one halts)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int k = find_start(S->astart, nl, t);
         const int l = S->alist[k];
@@ -245,7 +252,7 @@ batch_update_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *
         const double bs = block_sum(part, smem);
         if (threadIdx.x == 0) partials[t] = bs;
     }
-    if (!last_block_totals(partials, counter, nl, S->astart, tot)) return;
+    if (!last_block_totals(partials, counter, nl, S->astart, tot, nblk)) return;
     if (threadIdx.x != 0) return;
     S->iter += 1;
     S->trips += 1;
@@ -315,7 +322,7 @@ batch_ru_dslash_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S
         if (threadIdx.x == 0) partials[blockIdx.x] = bs;
         if (threadIdx.x == 0)  // per-lattice tile ranges of the full list
             for (int k = 0; k <= n; ++k) ident[k] = k < n ? descs[k].tile0 : descs[n - 1].tile0 + descs[n - 1].ntiles;
-        if (!last_block_totals(partials, counter, n, ident, tot)) return;
+        if (!last_block_totals(partials, counter, n, ident, tot, gridDim.x)) return;
         if (threadIdx.x != 0) return;
         for (int k = 0; k < n; ++k) {
             if (!need[k] || !S->need[k]) continue;
@@ -410,7 +417,7 @@ batch_norm2_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S, do
         partials[blockIdx.x] = bs;
         for (int k = 0; k <= n; ++k) ident[k] = k < n ? descs[k].tile0 : descs[n - 1].tile0 + descs[n - 1].ntiles;
     }
-    if (!last_block_totals(partials, counter, n, ident, tot)) return;
+    if (!last_block_totals(partials, counter, n, ident, tot, gridDim.x)) return;
     if (threadIdx.x != 0) return;
     for (int k = 0; k < n; ++k) {
         S->bb[k] = tot[k];
