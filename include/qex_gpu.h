@@ -246,17 +246,25 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  * ||b - A x|| / ||b|| <= tol, computed in FP64.
  *
  * inner = QEX_F64: plain CG in FP64 on fat64/lng64.
- * inner = QEX_F32, QEX_F32_R12 or QEX_F32_R12H: mixed precision: the CG iteration runs in
- *   FP32 on fat32/lng32 (fat32 in the `inner` link format, lng32 in QEX_F32;
- *   inner residual and iterate in FP32, all reductions in FP64);
+ * inner = QEX_F32, QEX_F32_R12, QEX_F32_R12H or QEX_F32_S16: mixed precision: the CG
+ *   iteration runs in FP32 on fat32/lng32 (fat32 in the `inner` link format,
+ *   lng32 in qex_long_links_prec(inner); inner residual and iterate in FP32,
+ *   all reductions in FP64);
  *   whenever the iterated residual norm drops below delta times its maximum
  *   since the last update (or meets tol), the FP64 solution is updated and the
  *   residual is recomputed in FP64 with fat64/lng64 (reliable update).
  * b64, x64: F64 even half fields; x64 holds the initial guess on entry and the
  *   solution on return.  lng64/lng32 NULL = no Naik term.
  * Synchronises the stream before returning (fills stats, may be NULL).
+ * Execution: one CUDA graph for the whole solve by default; for a mixed solve
+ * with Vh <= 32768 the inner iterations run instead as one persistent
+ * cooperative kernel between the reliable updates.  The environment variable
+ * QEX_CG_MODE = graph | host | fused forces one of the three.
  * Returns QEX_ERR_NOT_CONVERGED after maxiter iterations (x64 holds the last
- * iterate), QEX_ERR_NAN on a NaN/Inf or a non-positive <p, A p>. */
+ * iterate), QEX_ERR_NAN on a NaN/Inf or a non-positive <p, A p>,
+ * QEX_ERR_TIMEOUT if a grid barrier of the persistent kernel waited longer
+ * than about a second (blocks not co-resident; the kernel returns instead of
+ * waiting forever). */
 qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
                   const void *fat32, const void *lng32, double c_naik, double mass, const void *b64,
                   void *x64, double tol, int maxiter, double delta, void *stream,

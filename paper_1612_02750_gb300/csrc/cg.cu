@@ -15,9 +15,12 @@
 // kernel set the two conditions.  The loop ends when the true residual meets
 // tol, on the iteration cap, or on a NaN, and in any case after maxiter + 4
 // trips.  Setting QEX_CG_MODE=host instead enqueues batches of iterations
-// from the host and runs the reliable updates between batches.
+// from the host and runs the reliable updates between batches.  A mixed
+// solve of a small lattice (Vh <= 32768, or QEX_CG_MODE=fused) runs its inner
+// iterations as one persistent cooperative kernel instead (cg_fused.cu), with
+// the reliable updates launched from the host in between.
 //
-// Mixed precision (inner = F32 or F32_R12): x_hat, r_hat, p, A p live in FP32
+// Mixed precision (inner = any FP32 format): x_hat, r_hat, p, A p live in FP32
 // and the operator runs on FP32 links; when ||r_hat|| falls below delta times
 // its largest value since the last update, or meets tol, x += x_hat (FP64),
 // r = b - A x with the FP64 operator, r_hat = (float) r, and beta comes from
@@ -36,6 +39,10 @@ qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *
 void set_count_launches(bool on);
 
 static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Largest half volume that the mixed solve runs as the fused persistent
+// iteration by default (cg_fused.cu).
+constexpr int64_t kFusedAutoMaxVh = 32768;
 
 struct CgBuffers {
     double *r64, *tmp64, *p64[2], *ap64;
@@ -304,8 +311,11 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     qex_lattice *lat = const_cast<qex_lattice *>(latc);
     if ((st = ensure_scratch(lat))) return st;
     if (!lat->scalars_host2) QEX_CUDA(cudaMallocHost(&lat->scalars_host2, sizeof(CgScalars)));
+    // small lattices default to the persistent fused iteration (1.15-1.3x
+    // faster per iteration up to 16^4); QEX_CG_MODE=graph|host|fused forces
     const char *mode = getenv("QEX_CG_MODE");
-    const bool use_graph = !(mode && strcmp(mode, "host") == 0);
+    const bool use_fused = mixed && ((mode && strcmp(mode, "fused") == 0) || (!mode && lat->vh <= kFusedAutoMaxVh));
+    const bool use_graph = !(mode && (strcmp(mode, "host") == 0 || use_fused));
 
     Solve s;
     s.lat = lat;
@@ -399,6 +409,27 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
         cur = *h0;
         const unsigned long long rus = cur.reliable_updates > 1 ? cur.reliable_updates - 1 : 0;
         note_launches(G->kernels_per_trip * (unsigned long long)cur.trips + G->kernels_per_ru * rus);
+    } else if (!cur.done && !cur.halt && use_fused) {
+        // persistent inner iterations, FP64 reliable updates in between
+        while (!cur.done && !cur.error) {
+            if ((st = launch_cg_fused(lat, inner, s.fat32, s.lng32, s.c3, s.m2, s.B.xh32, s.B.r32, s.B.p32, s.B.ap32,
+                                      s.B.tmp32, cst)))
+                return st;
+            int timed_out = 0;
+            if ((st = fused_barrier_status(lat, cst, &timed_out))) return st;
+            if (timed_out) {
+                set_error("fused CG: a grid barrier timed out");
+                result = QEX_ERR_TIMEOUT;
+                break;
+            }
+            if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
+            cur = *h0;
+            if (cur.error || !cur.need_ru) break;
+            if ((st = enqueue_reliable_update(s, off, cst))) return st;
+            if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
+            cur = *h0;
+            if (!cur.done && !cur.error && cur.iters >= maxiter) break;
+        }
     } else if (!cur.done && !cur.halt) {
         const int batch = 8;
         while (!cur.done && !cur.error) {

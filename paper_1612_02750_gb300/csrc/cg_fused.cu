@@ -1,0 +1,277 @@
+// cg_fused.cu -- the mixed-precision CG iteration of a small lattice as one
+// persistent kernel.
+//
+// On a small lattice (a few thousand even sites) each of the three kernels of
+// an iteration does a few microseconds of work and the launch, the drain of
+// the grid and the last-block reduction tail cost as much again.  Here one
+// cooperative launch (every block resident) runs the inner iterations back to
+// back:
+//   1. tmp = D_oe (r + beta p_old) with p_new stored        grid barrier
+//   2. A p_new = m^2 p_new - D_eo tmp, block sums of <p,Ap>  grid barrier
+//      every block sums the block partials in the same fixed order -> alpha
+//   3. x += alpha p_new, r -= alpha A p_new, block sums of ||r||^2
+//                                                            grid barrier
+//      every block sums them -> beta, or the request for a reliable update
+// until a reliable update is due (or an error): then the kernel writes the CG
+// scalars back and returns, the host runs the FP64 reliable update with the
+// ordinary kernels, and launches it again.  The iterations are the ones the
+// three-kernel form computes (the reductions sum the same per-site terms in
+// another block grouping).
+//
+// Grid barriers: an arrival counter and a generation word, reset by the host
+// before each launch; the last block to arrive bumps the generation.  A wait
+// that lasts longer than about a second (clock64) records a timeout in the
+// error word and every block leaves at its next barrier, so a barrier can
+// never hang the GPU; the host then reports QEX_ERR_TIMEOUT.
+#include <math.h>
+
+#include "qex_dslash_site.cuh"
+#include "qex_kernels.cuh"
+
+namespace qex {
+
+template <typename R>
+struct FusedArgs {
+    Geom g;
+    const R *fat, *lng;
+    R c3, m2;
+    R *x, *r, *p0, *p1, *ap, *tmp;
+    CgScalars *S;
+    double *partials;            // 2 * gridDim.x
+    unsigned int *bar_count;     // arrivals at the current barrier
+    unsigned int *bar_gen;       // barriers completed in this launch
+    int *bar_err;                // nonzero: a barrier timed out
+};
+
+constexpr int kFusedBlock = 256;  // most threads per block (launch bounds)
+#ifndef QEX_FUSED_BLOCK
+#define QEX_FUSED_BLOCK 128  // threads per block of a launch (a sweep: 128 beats 256, 64, 32)
+#endif
+#ifndef QEX_FUSED_SPIN_NS
+#define QEX_FUSED_SPIN_NS 0  // sleep between polls of a barrier (0: poll back to back)
+#endif
+constexpr long long kBarrierTimeoutCycles = 2000000000ll;  // about one second at 2 GHz
+
+// Grid barrier number `gen + 1`; false if some block timed out (then every
+// block leaves at its next barrier).
+__device__ __forceinline__ bool fused_barrier(unsigned int *count, unsigned int *gen_word, int *err, unsigned int gen) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicExch(gen_word, gen + 1);
+        } else {
+            const long long t0 = clock64();
+            while (atomicAdd(gen_word, 0u) != gen + 1) {
+                if (atomicAdd(err, 0) != 0) break;
+                if (clock64() - t0 > kBarrierTimeoutCycles) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                if (QEX_FUSED_SPIN_NS > 0) __nanosleep(QEX_FUSED_SPIN_NS);
+            }
+        }
+        __threadfence();
+        ok = atomicAdd(err, 0) == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Sum of partials[0..n) in index order, returned to every thread of the block.
+__device__ __forceinline__ double fused_total(const double *partials, int n, double *smem) {
+    __shared__ double total;
+    const double s = block_sum_partials(partials, n, smem);
+    if (threadIdx.x == 0) total = s;
+    __syncthreads();
+    return total;
+}
+
+template <typename R, int FMT, bool NAIK>
+__global__ void __launch_bounds__(kFusedBlock, 2) cg_fused_kernel(const FusedArgs<R> A) {
+    __shared__ double smem[32];
+    CgScalars *S = A.S;
+    if (S->halt) return;  // uniform
+    const Geom &g = A.g;
+    const size_t vh = (size_t)g.vh;
+    const int nb = gridDim.x;
+    const int stride = nb * blockDim.x;
+    // the CG scalars, kept identical in every block (same sums, same order)
+    double rr = S->rr, beta = S->beta, rmax2 = S->rmax2, alpha = S->alpha, pAp = S->pAp;
+    int iters = S->iters, trips = S->trips;
+    const double stop2 = S->stop2, delta2 = S->delta2;
+    const int maxiter = S->maxiter;
+    int need_ru = 0, error = 0;
+    unsigned int gen = 0;
+    for (;;) {
+        const R *pold = (iters & 1) ? A.p1 : A.p0;
+        R *pnew = (iters & 1) ? A.p0 : A.p1;
+        const R b = (R)beta;
+        // 1. tmp = D_oe (r + beta p_old); p_new at the thread's own even index
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
+            const Site s = site_of(g, 1, i);
+            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, A.fat, A.lng, A.c3, 1, i, s,
+                                                          [&](int j) { return axpy_vec(A.r, pold, b, vh, j); });
+            store_vec(A.tmp, vh, i, acc);
+            store_vec(pnew, vh, i, axpy_vec(A.r, pold, b, vh, i));
+        }
+        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
+        // 2. A p_new = m^2 p_new - D_eo tmp; <p_new, A p_new>
+        double part = 0.0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
+            const Site s = site_of(g, 0, i);
+            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, A.fat, A.lng, A.c3, 0, i, s,
+                                                          [&](int j) { return load_vec((const R *)A.tmp, vh, j); });
+            const Vec3<R> qv = load_vec((const R *)pnew, vh, i);
+            Vec3<R> o;
+            R d = R(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o.c[a].re = fma(A.m2, qv.c[a].re, -acc.c[a].re);
+                o.c[a].im = fma(A.m2, qv.c[a].im, -acc.c[a].im);
+                d = fma(qv.c[a].re, o.c[a].re, d);
+                d = fma(qv.c[a].im, o.c[a].im, d);
+            }
+            store_vec(A.ap, vh, i, o);
+            part += (double)d;
+        }
+        {
+            const double bs = block_sum(part, smem);
+            if (threadIdx.x == 0) A.partials[blockIdx.x] = bs;
+        }
+        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
+        pAp = fused_total(A.partials, nb, smem);
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            error = isfinite(pAp) ? 2 : 1;
+            break;
+        }
+        alpha = rr / pAp;
+        // 3. x += alpha p_new; r -= alpha A p_new; ||r||^2
+        const R al = (R)alpha;
+        part = 0.0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
+            Vec3<R> xv = load_vec((const R *)A.x, vh, i), rv = load_vec((const R *)A.r, vh, i);
+            const Vec3<R> pv = load_vec((const R *)pnew, vh, i), av = load_vec((const R *)A.ap, vh, i);
+            R d = R(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xv.c[a].re = fma(al, pv.c[a].re, xv.c[a].re);
+                xv.c[a].im = fma(al, pv.c[a].im, xv.c[a].im);
+                rv.c[a].re = fma(-al, av.c[a].re, rv.c[a].re);
+                rv.c[a].im = fma(-al, av.c[a].im, rv.c[a].im);
+                d = fma(rv.c[a].re, rv.c[a].re, d);
+                d = fma(rv.c[a].im, rv.c[a].im, d);
+            }
+            store_vec(A.x, vh, i, xv);
+            store_vec(A.r, vh, i, rv);
+            part += (double)d;
+        }
+        {
+            const double bs = block_sum(part, smem);
+            if (threadIdx.x == 0) A.partials[nb + blockIdx.x] = bs;
+        }
+        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
+        const double rr_new = fused_total(A.partials + nb, nb, smem);
+        iters += 1;
+        trips += 1;
+        if (!isfinite(rr_new)) {
+            error = 1;
+            break;
+        }
+        if (rr_new > rmax2) rmax2 = rr_new;
+        if (rr_new <= stop2 || rr_new < delta2 * rmax2 || iters >= maxiter) {
+            need_ru = 1;  // rr keeps its value: beta then comes from the true residual
+            break;
+        }
+        beta = rr_new / rr;
+        rr = rr_new;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S->rr = rr;
+        S->beta = beta;
+        S->rmax2 = rmax2;
+        S->alpha = alpha;
+        S->pAp = pAp;
+        S->iters = iters;
+        S->trips = trips;
+        if (error) S->error = error;
+        S->need_ru = need_ru;
+        S->halt = 1;
+    }
+}
+
+template <typename R, int FMT, bool NAIK>
+static qex_status launch_fused_t(qex_lattice *lat, const FusedArgs<R> &A0, cudaStream_t st) {
+    auto kernel = cg_fused_kernel<R, FMT, NAIK>;
+    int per_sm = 0;
+    const int block = QEX_FUSED_BLOCK;
+    QEX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0));
+    if (per_sm < 1) {
+        set_error("the fused CG kernel does not fit on an SM");
+        return QEX_ERR_CUDA;
+    }
+    const int want = blocks_for(lat->vh, block);
+    const int cap = per_sm * sm_count();
+    int nb = want < cap ? want : cap;
+    if ((size_t)lat->partials_len < 2 * (size_t)nb) {
+        set_error("internal: partials buffer too small for the fused CG kernel");
+        return QEX_ERR_ARG;
+    }
+    FusedArgs<R> A = A0;
+    // fresh barrier state for this launch (counter[1..3] of the lattice scratch)
+    QEX_CUDA(cudaMemsetAsync(lat->counter + 1, 0, 3 * sizeof(unsigned int), st));
+    A.partials = lat->partials;
+    A.bar_count = lat->counter + 1;
+    A.bar_gen = lat->counter + 2;
+    A.bar_err = reinterpret_cast<int *>(lat->counter + 3);
+    void *args[] = {&A};
+    QEX_CUDA(cudaLaunchCooperativeKernel((const void *)kernel, dim3(nb), dim3(block), args, 0, st));
+    note_launch();
+    return QEX_OK;
+}
+
+template <int FMT>
+static qex_status launch_fused_n(qex_lattice *lat, const FusedArgs<float> &A, bool naik, cudaStream_t st) {
+    return naik ? launch_fused_t<float, FMT, true>(lat, A, st) : launch_fused_t<float, FMT, false>(lat, A, st);
+}
+
+// One run of the fused iteration kernel (mixed precision only).
+qex_status launch_cg_fused(qex_lattice *lat, qex_prec inner, const void *fat32, const void *lng32, double c3, double m2,
+                           float *x, float *r, float *const p[2], float *ap, float *tmp, cudaStream_t st) {
+    FusedArgs<float> A = {};
+    A.g = lat->geom;
+    A.fat = (const float *)fat32;
+    A.lng = (const float *)lng32;
+    A.c3 = (float)c3;
+    A.m2 = (float)m2;
+    A.x = x;
+    A.r = r;
+    A.p0 = p[0];
+    A.p1 = p[1];
+    A.ap = ap;
+    A.tmp = tmp;
+    A.S = lat->scalars;
+    const bool naik = lng32 != nullptr;
+    switch (inner) {
+        case QEX_F32: return launch_fused_n<0>(lat, A, naik, st);
+        case QEX_F32_R12: return launch_fused_n<1>(lat, A, naik, st);
+        case QEX_F32_R12H: return launch_fused_n<2>(lat, A, naik, st);
+        case QEX_F32_S16: return launch_fused_n<3>(lat, A, naik, st);
+        default: set_error("the fused CG iteration is for mixed precision only"); return QEX_ERR_ARG;
+    }
+}
+
+// Whether a barrier of the last fused run timed out (reads the error word).
+qex_status fused_barrier_status(qex_lattice *lat, cudaStream_t st, int *timed_out) {
+    int v = 0;
+    QEX_CUDA(cudaMemcpyAsync(&v, lat->counter + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QEX_CUDA(cudaStreamSynchronize(st));
+    *timed_out = v != 0;
+    return QEX_OK;
+}
+
+}  // namespace qex
