@@ -18,8 +18,9 @@
 // three-kernel form computes (the reductions sum the same per-site terms in
 // another block grouping).
 //
-// Grid barriers: an arrival counter and a generation word, reset by the host
-// before each launch; the last block to arrive bumps the generation.  A wait
+// Grid barriers: arrival counters (per group of 32 blocks, then across the
+// groups) and a generation word, reset by the host before each launch; the
+// last block to arrive bumps the generation.  A wait
 // that lasts longer than about a second (clock64) records a timeout in the
 // error word and every block leaves at its next barrier, so a barrier can
 // never hang the GPU; the host then reports QEX_ERR_TIMEOUT.
@@ -38,7 +39,7 @@ struct FusedArgs {
     R *x, *r, *p0, *p1, *ap, *tmp;
     CgScalars *S;
     double *partials;            // 2 * gridDim.x
-    unsigned int *bar_count;     // arrivals at the current barrier
+    unsigned int *bar_count;     // barrier counters: top at [0], group g at [(g + 1) * 32]
     unsigned int *bar_gen;       // barriers completed in this launch
     int *bar_err;                // nonzero: a barrier timed out
 };
@@ -53,21 +54,39 @@ constexpr int kFusedBlock = 256;  // most threads per block (launch bounds)
 constexpr long long kBarrierTimeoutCycles = 2000000000ll;  // about one second at 2 GHz
 
 // Grid barrier number `gen + 1`; false if some block timed out (then every
-// block leaves at its next barrier).
-__device__ __forceinline__ bool fused_barrier(unsigned int *count, unsigned int *gen_word, int *err, unsigned int gen) {
+// block leaves at its next barrier).  Two levels: a block arrives at the
+// counter of its group of 32 blocks (each counter on its own 128-byte line);
+// the last of a group arrives at the top counter, and the last of those bumps
+// the generation.  Waiting blocks poll the generation with plain loads, so
+// the arrivals' atomics meet no contention from the pollers.
+constexpr int kBarrierGroup = 32;
+constexpr int kBarrierStride = 32;  // unsigned words between counters (128 bytes)
+
+__device__ __forceinline__ bool fused_barrier(unsigned int *counters, unsigned int *gen_word, int *err,
+                                              unsigned int gen) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned int arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicExch(gen_word, gen + 1);
-        } else {
+        const int grp = blockIdx.x / kBarrierGroup, ngroups = (gridDim.x + kBarrierGroup - 1) / kBarrierGroup;
+        const unsigned int gsize = min((unsigned int)kBarrierGroup, gridDim.x - grp * kBarrierGroup);
+        unsigned int *gc = counters + (size_t)(grp + 1) * kBarrierStride;
+        bool last = false;
+        if (atomicAdd(gc, 1u) == gsize - 1) {
+            atomicExch(gc, 0u);
+            if (atomicAdd(counters, 1u) == (unsigned int)ngroups - 1) {
+                atomicExch(counters, 0u);
+                __threadfence();
+                atomicExch(gen_word, gen + 1);
+                last = true;
+            }
+        }
+        if (!last) {
+            const volatile unsigned int *gv = gen_word;
+            const volatile int *ev = err;
             const long long t0 = clock64();
-            while (atomicAdd(gen_word, 0u) != gen + 1) {
-                if (atomicAdd(err, 0) != 0) break;
+            while (*gv != gen + 1) {
+                if (*ev != 0) break;
                 if (clock64() - t0 > kBarrierTimeoutCycles) {
                     atomicExch(err, 1);
                     break;
@@ -76,10 +95,38 @@ __device__ __forceinline__ bool fused_barrier(unsigned int *count, unsigned int 
             }
         }
         __threadfence();
-        ok = atomicAdd(err, 0) == 0;
+        ok = *(const volatile int *)err == 0;
     }
     __syncthreads();
     return ok != 0;
+}
+
+// Vectors written by this kernel are read back in later phases of the same
+// launch, so they are loaded through L2 (ld.global.cg), never through the
+// read-only path that assumes data constant for the kernel's lifetime; only
+// the links use that path.
+__device__ __forceinline__ Vec3<float> load_vec_cg(const float *base, size_t vh, int i) {
+    const float4 t = __ldcg(reinterpret_cast<const float4 *>(base) + i);
+    const float2 u = __ldcg(reinterpret_cast<const float2 *>(base + 4 * vh) + i);
+    Vec3<float> v;
+    v.c[0].re = t.x;
+    v.c[0].im = t.y;
+    v.c[1].re = t.z;
+    v.c[1].im = t.w;
+    v.c[2].re = u.x;
+    v.c[2].im = u.y;
+    return v;
+}
+
+__device__ __forceinline__ Vec3<float> axpy_vec_cg(const float *r, const float *p, float beta, size_t vh, int j) {
+    const Vec3<float> rv = load_vec_cg(r, vh, j), pv = load_vec_cg(p, vh, j);
+    Vec3<float> v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        v.c[a].re = fmaf(beta, pv.c[a].re, rv.c[a].re);
+        v.c[a].im = fmaf(beta, pv.c[a].im, rv.c[a].im);
+    }
+    return v;
 }
 
 // Sum of partials[0..n) in index order, returned to every thread of the block.
@@ -91,115 +138,145 @@ __device__ __forceinline__ double fused_total(const double *partials, int n, dou
     return total;
 }
 
+#ifndef QEX_FUSED_MIN_BLOCKS
+#define QEX_FUSED_MIN_BLOCKS 2  // launch-bounds residency of 256-thread blocks (register cap)
+#endif
+
+// Loop state of the solve, identical in every block, kept in shared memory so
+// that it holds no registers during the Dslash phases.
+struct FusedState {
+    double rr, beta, rmax2, alpha, pAp;
+    int iters, trips, need_ru, error;
+};
+
 template <typename R, int FMT, bool NAIK>
-__global__ void __launch_bounds__(kFusedBlock, 2) cg_fused_kernel(const FusedArgs<R> A) {
+__global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_kernel(const FusedArgs<R> A) {
     __shared__ double smem[32];
+    __shared__ FusedState st;
     CgScalars *S = A.S;
     if (S->halt) return;  // uniform
     const Geom &g = A.g;
     const size_t vh = (size_t)g.vh;
     const int nb = gridDim.x;
     const int stride = nb * blockDim.x;
-    // the CG scalars, kept identical in every block (same sums, same order)
-    double rr = S->rr, beta = S->beta, rmax2 = S->rmax2, alpha = S->alpha, pAp = S->pAp;
-    int iters = S->iters, trips = S->trips;
-    const double stop2 = S->stop2, delta2 = S->delta2;
-    const int maxiter = S->maxiter;
-    int need_ru = 0, error = 0;
+    if (threadIdx.x == 0) {
+        st.rr = S->rr;
+        st.beta = S->beta;
+        st.rmax2 = S->rmax2;
+        st.alpha = S->alpha;
+        st.pAp = S->pAp;
+        st.iters = S->iters;
+        st.trips = S->trips;
+        st.need_ru = 0;
+        st.error = 0;
+    }
+    __syncthreads();
     unsigned int gen = 0;
     for (;;) {
-        const R *pold = (iters & 1) ? A.p1 : A.p0;
-        R *pnew = (iters & 1) ? A.p0 : A.p1;
-        const R b = (R)beta;
-        // 1. tmp = D_oe (r + beta p_old); p_new at the thread's own even index
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
-            const Site s = site_of(g, 1, i);
-            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, A.fat, A.lng, A.c3, 1, i, s,
-                                                          [&](int j) { return axpy_vec(A.r, pold, b, vh, j); });
-            store_vec(A.tmp, vh, i, acc);
-            store_vec(pnew, vh, i, axpy_vec(A.r, pold, b, vh, i));
+        const int it = st.iters;
+        const R *pold = (it & 1) ? A.p1 : A.p0;
+        R *pnew = (it & 1) ? A.p0 : A.p1;
+        {   // 1. tmp = D_oe (r + beta p_old); p_new at the thread's own even index
+            const R b = (R)st.beta;
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
+                const Site s = site_of(g, 1, i);
+                const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, A.fat, A.lng, A.c3, 1, i, s,
+                                                              [&](int j) { return axpy_vec_cg(A.r, pold, b, vh, j); });
+                store_vec(A.tmp, vh, i, acc);
+                store_vec(pnew, vh, i, axpy_vec_cg(A.r, pold, b, vh, i));
+            }
         }
         if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
-        // 2. A p_new = m^2 p_new - D_eo tmp; <p_new, A p_new>
-        double part = 0.0;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
-            const Site s = site_of(g, 0, i);
-            const Vec3<R> acc = dslash_site<R, FMT, NAIK>(g, A.fat, A.lng, A.c3, 0, i, s,
-                                                          [&](int j) { return load_vec((const R *)A.tmp, vh, j); });
-            const Vec3<R> qv = load_vec((const R *)pnew, vh, i);
-            Vec3<R> o;
-            R d = R(0);
+        {   // 2. A p_new = m^2 p_new - D_eo tmp; <p_new, A p_new>
+            double part = 0.0;
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
+                const Site s = site_of(g, 0, i);
+                const Vec3<R> acc = dslash_site<R, FMT, NAIK>(
+                    g, A.fat, A.lng, A.c3, 0, i, s, [&](int j) { return load_vec_cg(A.tmp, vh, j); });
+                const Vec3<R> qv = load_vec_cg(pnew, vh, i);
+                Vec3<R> o;
+                R d = R(0);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                o.c[a].re = fma(A.m2, qv.c[a].re, -acc.c[a].re);
-                o.c[a].im = fma(A.m2, qv.c[a].im, -acc.c[a].im);
-                d = fma(qv.c[a].re, o.c[a].re, d);
-                d = fma(qv.c[a].im, o.c[a].im, d);
+                for (int a = 0; a < 3; ++a) {
+                    o.c[a].re = fma(A.m2, qv.c[a].re, -acc.c[a].re);
+                    o.c[a].im = fma(A.m2, qv.c[a].im, -acc.c[a].im);
+                    d = fma(qv.c[a].re, o.c[a].re, d);
+                    d = fma(qv.c[a].im, o.c[a].im, d);
+                }
+                store_vec(A.ap, vh, i, o);
+                part += (double)d;
             }
-            store_vec(A.ap, vh, i, o);
-            part += (double)d;
-        }
-        {
             const double bs = block_sum(part, smem);
             if (threadIdx.x == 0) A.partials[blockIdx.x] = bs;
         }
         if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
-        pAp = fused_total(A.partials, nb, smem);
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-            error = isfinite(pAp) ? 2 : 1;
-            break;
-        }
-        alpha = rr / pAp;
-        // 3. x += alpha p_new; r -= alpha A p_new; ||r||^2
-        const R al = (R)alpha;
-        part = 0.0;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
-            Vec3<R> xv = load_vec((const R *)A.x, vh, i), rv = load_vec((const R *)A.r, vh, i);
-            const Vec3<R> pv = load_vec((const R *)pnew, vh, i), av = load_vec((const R *)A.ap, vh, i);
-            R d = R(0);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xv.c[a].re = fma(al, pv.c[a].re, xv.c[a].re);
-                xv.c[a].im = fma(al, pv.c[a].im, xv.c[a].im);
-                rv.c[a].re = fma(-al, av.c[a].re, rv.c[a].re);
-                rv.c[a].im = fma(-al, av.c[a].im, rv.c[a].im);
-                d = fma(rv.c[a].re, rv.c[a].re, d);
-                d = fma(rv.c[a].im, rv.c[a].im, d);
-            }
-            store_vec(A.x, vh, i, xv);
-            store_vec(A.r, vh, i, rv);
-            part += (double)d;
-        }
         {
+            const double pAp = fused_total(A.partials, nb, smem);
+            if (threadIdx.x == 0) {
+                st.pAp = pAp;
+                if (!(pAp > 0.0) || !isfinite(pAp))
+                    st.error = isfinite(pAp) ? 2 : 1;
+                else
+                    st.alpha = st.rr / pAp;
+            }
+            __syncthreads();
+            if (st.error) break;
+        }
+        {   // 3. x += alpha p_new; r -= alpha A p_new; ||r||^2
+            const R al = (R)st.alpha;
+            double part = 0.0;
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
+                Vec3<R> xv = load_vec_cg(A.x, vh, i), rv = load_vec_cg(A.r, vh, i);
+                const Vec3<R> pv = load_vec_cg(pnew, vh, i), av = load_vec_cg(A.ap, vh, i);
+                R d = R(0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    xv.c[a].re = fma(al, pv.c[a].re, xv.c[a].re);
+                    xv.c[a].im = fma(al, pv.c[a].im, xv.c[a].im);
+                    rv.c[a].re = fma(-al, av.c[a].re, rv.c[a].re);
+                    rv.c[a].im = fma(-al, av.c[a].im, rv.c[a].im);
+                    d = fma(rv.c[a].re, rv.c[a].re, d);
+                    d = fma(rv.c[a].im, rv.c[a].im, d);
+                }
+                store_vec(A.x, vh, i, xv);
+                store_vec(A.r, vh, i, rv);
+                part += (double)d;
+            }
             const double bs = block_sum(part, smem);
             if (threadIdx.x == 0) A.partials[nb + blockIdx.x] = bs;
         }
         if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
-        const double rr_new = fused_total(A.partials + nb, nb, smem);
-        iters += 1;
-        trips += 1;
-        if (!isfinite(rr_new)) {
-            error = 1;
-            break;
+        {
+            const double rr_new = fused_total(A.partials + nb, nb, smem);
+            if (threadIdx.x == 0) {
+                st.iters += 1;
+                st.trips += 1;
+                if (!isfinite(rr_new)) {
+                    st.error = 1;
+                } else {
+                    if (rr_new > st.rmax2) st.rmax2 = rr_new;
+                    if (rr_new <= S->stop2 || rr_new < S->delta2 * st.rmax2 || st.iters >= S->maxiter) {
+                        st.need_ru = 1;  // rr keeps its value: beta then comes from the true residual
+                    } else {
+                        st.beta = rr_new / st.rr;
+                        st.rr = rr_new;
+                    }
+                }
+            }
+            __syncthreads();
+            if (st.error || st.need_ru) break;
         }
-        if (rr_new > rmax2) rmax2 = rr_new;
-        if (rr_new <= stop2 || rr_new < delta2 * rmax2 || iters >= maxiter) {
-            need_ru = 1;  // rr keeps its value: beta then comes from the true residual
-            break;
-        }
-        beta = rr_new / rr;
-        rr = rr_new;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        S->rr = rr;
-        S->beta = beta;
-        S->rmax2 = rmax2;
-        S->alpha = alpha;
-        S->pAp = pAp;
-        S->iters = iters;
-        S->trips = trips;
-        if (error) S->error = error;
-        S->need_ru = need_ru;
+        S->rr = st.rr;
+        S->beta = st.beta;
+        S->rmax2 = st.rmax2;
+        S->alpha = st.alpha;
+        S->pAp = st.pAp;
+        S->iters = st.iters;
+        S->trips = st.trips;
+        if (st.error) S->error = st.error;
+        S->need_ru = st.need_ru;
         S->halt = 1;
     }
 }
@@ -217,16 +294,24 @@ static qex_status launch_fused_t(qex_lattice *lat, const FusedArgs<R> &A0, cudaS
     const int want = blocks_for(lat->vh, block);
     const int cap = per_sm * sm_count();
     int nb = want < cap ? want : cap;
-    if ((size_t)lat->partials_len < 2 * (size_t)nb) {
+    // barrier words after the 2 nb partial sums in the lattice's partials
+    // buffer: the top and group counters (128 bytes apart), then the
+    // generation; the error word is counter[3] of the lattice scratch; all
+    // fresh for every launch
+    const int ngroups = (nb + kBarrierGroup - 1) / kBarrierGroup;
+    const size_t bar_words = (size_t)(ngroups + 1) * kBarrierStride + kBarrierStride;
+    const size_t need = 2 * (size_t)nb + (bar_words * sizeof(unsigned int) + sizeof(double) - 1) / sizeof(double) + 16;
+    if ((size_t)lat->partials_len < need) {
         set_error("internal: partials buffer too small for the fused CG kernel");
         return QEX_ERR_ARG;
     }
+    unsigned int *bar = reinterpret_cast<unsigned int *>(lat->partials + 2 * (size_t)nb + 16);
+    QEX_CUDA(cudaMemsetAsync(bar, 0, bar_words * sizeof(unsigned int), st));
+    QEX_CUDA(cudaMemsetAsync(lat->counter + 3, 0, sizeof(unsigned int), st));
     FusedArgs<R> A = A0;
-    // fresh barrier state for this launch (counter[1..3] of the lattice scratch)
-    QEX_CUDA(cudaMemsetAsync(lat->counter + 1, 0, 3 * sizeof(unsigned int), st));
     A.partials = lat->partials;
-    A.bar_count = lat->counter + 1;
-    A.bar_gen = lat->counter + 2;
+    A.bar_count = bar;
+    A.bar_gen = bar + (size_t)(ngroups + 1) * kBarrierStride;
     A.bar_err = reinterpret_cast<int *>(lat->counter + 3);
     void *args[] = {&A};
     QEX_CUDA(cudaLaunchCooperativeKernel((const void *)kernel, dim3(nb), dim3(block), args, 0, st));
