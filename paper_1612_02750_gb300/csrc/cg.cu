@@ -87,6 +87,13 @@ struct Solve {
     CgBuffers B;
 };
 
+#ifndef QEX_REVERSE_SECOND
+#define QEX_REVERSE_SECOND 1
+#endif
+// The normal-operator Dslash walks the sites downwards, meeting first the
+// links the D_oe launch before it read last (still in L2).
+static const bool reverse_second = QEX_REVERSE_SECOND != 0;
+
 // One CG iteration in the inner precision, every kernel halt-checked.
 static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t st) {
     qex_lattice *lat = s.lat;
@@ -128,6 +135,7 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
     a.epi = EPI_NORMAL;
     a.psel = 1;
     a.m2 = s.m2;
+    a.reverse = reverse_second ? 1 : 0;
     if ((err = launch_dslash(lat, a, st))) return err;
     return launch_update_xr(lat, a.prec, x, r, pb, ap, S, ctl, st);
 }

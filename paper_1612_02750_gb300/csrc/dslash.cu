@@ -33,6 +33,7 @@ struct DsParams {
     R *pbuf0, *pbuf1;   // p ping-pong
     int psel;
     int skip_zero_x;
+    int reverse;        // walk the sites from the last index down
     double *partials;
     unsigned int *counter;
 };
@@ -66,7 +67,8 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     double part = 0.0;
     // grid-stride over the sites: one pass per thread when the grid covers
     // the lattice, several when the launch is persistent (reducing variants)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.vh; k += gridDim.x * blockDim.x) {
+        const int i = P.reverse ? g.vh - 1 - k : k;
         const Site s = site_of(g, p, i);
         Vec3<R> acc;
         if (EPI == EPI_RESID && zero_x) {
@@ -210,6 +212,7 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.pbuf1 = (R *)a.pbuf[1];
     P.psel = a.psel;
     P.skip_zero_x = a.skip_zero_x;
+    P.reverse = a.reverse;
     P.partials = lat->partials;
     P.counter = lat->counter;
     int grid, block;

@@ -65,6 +65,8 @@ struct DslashArgs {
     const void *r;       // EPI_PUPD
     void *pbuf[2];       // EPI_PUPD, and EPI_PLAIN / EPI_NORMAL when psel
     int psel;            // EPI_PLAIN: in = p_new; EPI_NORMAL: q = p_new
+    int reverse;         // visit the sites from the last index down (the second Dslash of a CG
+                         // iteration meets the links the first one read last while they are in L2)
     int skip_zero_x;     // EPI_PLAIN / EPI_RESID of the first residual: unless S->x_nonzero,
                          // PLAIN writes nothing and RESID takes D in = 0 (r = b)
 };
