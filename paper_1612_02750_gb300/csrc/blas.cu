@@ -55,7 +55,7 @@ __device__ __forceinline__ void set_conditions(const GraphCtl &ctl, unsigned int
 // (iterated residual small enough, or the iteration cap reached), or stop
 // on a NaN.  In the graph solve the last block also sets the loop and
 // reliable-update conditions; a halted entry clears both.
-template <typename R>
+template <typename R, bool DO_X>
 __global__ void __launch_bounds__(kBlock)
 update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf1, const R *__restrict__ ap,
                  CgScalars *S, double *partials, unsigned int *counter, const GraphCtl ctl) {
@@ -73,16 +73,23 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf
     const R *p = (S->iters & 1) ? pbuf0 : pbuf1;  // the new direction
     double part = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
-        Vec3<R> xv = load_vec(x, vh, i), rv = load_vec(r, vh, i);
-        const Vec3<R> pv = load_vec(p, vh, i), av = load_vec(ap, vh, i);
+        Vec3<R> rv = load_vec(r, vh, i);
+        const Vec3<R> av = load_vec(ap, vh, i);
+        if constexpr (DO_X) {
+            Vec3<R> xv = load_vec(x, vh, i);
+            const Vec3<R> pv = load_vec(p, vh, i);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
+                xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
+            }
+            store_vec(x, vh, i, xv);
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
-            xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
             rv.c[a].re = fma(-alpha, av.c[a].re, rv.c[a].re);
             rv.c[a].im = fma(-alpha, av.c[a].im, rv.c[a].im);
         }
-        store_vec(x, vh, i, xv);
         store_vec(r, vh, i, rv);
         part += (double)norm2_site(rv);
     }
@@ -133,13 +140,26 @@ update_p_kernel(int vh, const R *__restrict__ r, R *pbuf0, R *pbuf1, const CgSca
     }
 }
 
-// x64 += xh32; xh32 = 0
-__global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restrict__ x, float *__restrict__ xh) {
+// x64 += xh32 + alpha p (the iterate update the last iteration left pending,
+// p = pbuf[iters & 1]; pbuf0 NULL: none); xh32 = 0
+__global__ void __launch_bounds__(kBlock)
+accum_x_kernel(int vh, double *__restrict__ x, float *__restrict__ xh, const float *pbuf0, const float *pbuf1,
+               const CgScalars *S) {
     pdl_trigger();
     pdl_wait();
+    const float *p = pbuf0 ? ((S->iters & 1) ? pbuf1 : pbuf0) : nullptr;
+    const float alpha = p ? (float)S->alpha : 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
         Vec3<double> xv = load_vec(x, vh, i);
-        const Vec3<float> hv = load_vec(xh, vh, i);
+        Vec3<float> hv = load_vec(xh, vh, i);
+        if (p) {  // the same FP32 step the iteration would have taken
+            const Vec3<float> pv = load_vec(p, vh, i);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                hv.c[a].re = fmaf(alpha, pv.c[a].re, hv.c[a].re);
+                hv.c[a].im = fmaf(alpha, pv.c[a].im, hv.c[a].im);
+            }
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             xv.c[a].re += (double)hv.c[a].re;
@@ -156,10 +176,13 @@ __global__ void __launch_bounds__(kBlock) accum_x_kernel(int vh, double *__restr
 // End of a reliable update: r32 = (float) r64 (mixed precision only), and
 // in the graph solve the loop condition from the flags the FP64 residual set.
 __global__ void __launch_bounds__(kBlock)
-finish_ru_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32, const CgScalars *S,
+finish_ru_kernel(int vh, const double *__restrict__ r64, float *__restrict__ r32, CgScalars *S,
                  const GraphCtl ctl) {
     pdl_trigger();
     pdl_wait();
+    // nothing is pending for the iterate after a reliable update (no block
+    // of this kernel reads alpha)
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->alpha = 0.0;
     if (r32) {
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < vh; i += gridDim.x * blockDim.x) {
             const Vec3<double> rd = load_vec(r64, vh, i);
@@ -254,11 +277,17 @@ qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, v
                             CgScalars *S, const GraphCtl &ctl, cudaStream_t st) {
     int nb = blas_blocks(lat), vh = (int)lat->vh;
     if (prec == QEX_F64)
-        launch_k(update_xr_kernel<double>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (double *)x, (double *)r,
-                 (double *)pbuf[0], (double *)pbuf[1], (const double *)ap, S, lat->partials, lat->counter, ctl);
+        launch_k(update_xr_kernel<double, true>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (double *)x,
+                 (double *)r, (double *)pbuf[0], (double *)pbuf[1], (const double *)ap, S, lat->partials,
+                 lat->counter, ctl);
+    else if (x)
+        launch_k(update_xr_kernel<float, true>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (float *)x,
+                 (float *)r, (float *)pbuf[0], (float *)pbuf[1], (const float *)ap, S, lat->partials, lat->counter,
+                 ctl);
     else
-        launch_k(update_xr_kernel<float>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (float *)x, (float *)r,
-                 (float *)pbuf[0], (float *)pbuf[1], (const float *)ap, S, lat->partials, lat->counter, ctl);
+        launch_k(update_xr_kernel<float, false>, dim3(nb), dim3(kBlock), 0, st, lat->pdl != 0, vh, (float *)x,
+                 (float *)r, (float *)pbuf[0], (float *)pbuf[1], (const float *)ap, S, lat->partials, lat->counter,
+                 ctl);
     QEX_CHECK_LAUNCH("update_xr_kernel");
     return QEX_OK;
 }
@@ -276,14 +305,16 @@ qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void 
     return QEX_OK;
 }
 
-qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st) {
-    launch_k(accum_x_kernel, dim3(blas_blocks(lat)), dim3(kBlock), 0, st, lat->pdl != 0, (int)lat->vh, x64, xh32);
+qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, float *const pbuf[2], const CgScalars *S,
+                          cudaStream_t st) {
+    launch_k(accum_x_kernel, dim3(blas_blocks(lat)), dim3(kBlock), 0, st, lat->pdl != 0, (int)lat->vh, x64, xh32,
+             (const float *)(pbuf ? pbuf[0] : nullptr), (const float *)(pbuf ? pbuf[1] : nullptr), S);
     QEX_CHECK_LAUNCH("accum_x_kernel");
     return QEX_OK;
 }
 
-qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, const CgScalars *S,
-                            const GraphCtl &ctl, cudaStream_t st) {
+qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, CgScalars *S, const GraphCtl &ctl,
+                            cudaStream_t st) {
     launch_k(finish_ru_kernel, dim3(r32 ? blas_blocks(lat) : 1), dim3(kBlock), 0, st, lat->pdl != 0, (int)lat->vh, r64,
              r32, S, ctl);
     QEX_CHECK_LAUNCH("finish_ru_kernel");

@@ -8,6 +8,10 @@
 //      pass, because its Dslash is FP64-ALU bound);
 //   2. A p_new = m^2 p_new - D_eo tmp with <p_new, A p_new> -> alpha;
 //   3. x += alpha p_new, r -= alpha A p_new, ||r||^2 -> beta or a halt flag.
+// In a mixed solve the iterate update of kernel 3 moves into the next
+// iteration's kernel 1, which reads p_old at its own site anyway (kernel 3
+// then moves r and A p only); a reliable update takes the pending alpha p
+// itself and zeroes alpha.
 // alpha, beta and the norms stay in device memory.  By default the whole
 // solve runs as one CUDA graph: a conditional WHILE node around the three
 // kernels, followed inside the loop by a conditional IF node holding the
@@ -84,9 +88,13 @@ struct Solve {
     double c3, m2;
     const double *b64;
     double *x64;
+    bool defer_x;  // the FP32 iterate takes alpha p one iteration late, in kernel 1
     CgBuffers B;
 };
 
+#ifndef QEX_DEFER_X
+#define QEX_DEFER_X 1
+#endif
 #ifndef QEX_REVERSE_SECOND
 #define QEX_REVERSE_SECOND 1
 #endif
@@ -121,6 +129,10 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
         // FP32: the direction update rides along the first Dslash (its few
         // extra FMAs per neighbour are free in a memory-bound kernel)
         a.epi = EPI_PUPD;
+        if (s.defer_x) {
+            a.x = x;
+            x = nullptr;
+        }
     } else {
         // FP64: the Dslash is FP64-ALU bound, so the update is its own
         // memory-bound pass instead of eight recomputations per site
@@ -148,7 +160,8 @@ static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStr
     qex_lattice *lat = s.lat;
     CgScalars *S = lat->scalars;
     qex_status err;
-    if (s.mixed && (err = launch_accum_x(lat, s.x64, s.B.xh32, st))) return err;
+    if (s.mixed && (err = launch_accum_x(lat, s.x64, s.B.xh32, (s.defer_x && !first) ? s.B.p32 : nullptr, S, st)))
+        return err;
     DslashArgs a = {};
     a.prec = QEX_F64;
     a.fat = s.fat64;
@@ -337,6 +350,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     s.m2 = mass * mass;
     s.b64 = (const double *)b64;
     s.x64 = (double *)x64;
+    s.defer_x = mixed && !use_fused && QEX_DEFER_X != 0;  // the fused kernel updates x itself
     const cudaStream_t cst = as_stream(stream);
     // launch shapes of the inner iteration and of the FP64 reliable updates,
     // before the graph bakes them in (the vector kernels keep their compiled

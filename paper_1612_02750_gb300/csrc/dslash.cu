@@ -30,6 +30,7 @@ struct DsParams {
     CgScalars *S;
     int check_halt;
     const R *r;         // EPI_PUPD
+    R *x;               // EPI_PUPD: iterate that takes the pending alpha p_old (NULL: none)
     R *pbuf0, *pbuf1;   // p ping-pong
     int psel;
     int skip_zero_x;
@@ -58,7 +59,9 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     R beta = R(0);
     const R *in = P.in;
     if (EPI == EPI_PLAIN && P.psel) in = (P.S->iters & 1) ? P.pbuf0 : P.pbuf1;  // the new direction
+    R alpha = R(0);
     if constexpr (EPI == EPI_PUPD) {
+        alpha = (R)P.S->alpha;
         const int it = P.S->iters;
         pold = (it & 1) ? P.pbuf1 : P.pbuf0;
         pnew = (it & 1) ? P.pbuf0 : P.pbuf1;
@@ -86,8 +89,26 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
             store_vec(P.out, vh, i, acc);
         } else if constexpr (EPI == EPI_PUPD) {
             store_vec(P.out, vh, i, acc);
-            // this thread also owns index i of the other parity's direction
-            store_vec(pnew, vh, i, axpy_vec(P.r, pold, beta, vh, i));
+            // this thread also owns index i of the other parity's direction,
+            // and of the iterate, which takes the previous iteration's alpha p
+            // (p_old read once for both; the same FMAs as axpy_vec)
+            const Vec3<R> pv = load_vec(pold, vh, i), rv = load_vec(P.r, vh, i);
+            Vec3<R> pn;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                pn.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+                pn.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+            }
+            store_vec(pnew, vh, i, pn);
+            if (P.x) {
+                Vec3<R> xv = load_vec(P.x, vh, i);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    xv.c[a].re = fma(alpha, pv.c[a].re, xv.c[a].re);
+                    xv.c[a].im = fma(alpha, pv.c[a].im, xv.c[a].im);
+                }
+                store_vec(P.x, vh, i, xv);
+            }
         } else if constexpr (EPI == EPI_NORMAL) {
             // out = m^2 q - D in;  part = Re <q, out>
             const R *q = P.q;
@@ -208,6 +229,7 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.S = a.S;
     P.check_halt = a.check_halt;
     P.r = (const R *)a.r;
+    P.x = (R *)a.x;
     P.pbuf0 = (R *)a.pbuf[0];
     P.pbuf1 = (R *)a.pbuf[1];
     P.psel = a.psel;

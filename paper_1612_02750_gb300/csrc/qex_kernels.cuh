@@ -63,6 +63,7 @@ struct DslashArgs {
     int check_halt;
     // CG direction ping-pong: p_old = pbuf[iters & 1], p_new = pbuf[(iters + 1) & 1]
     const void *r;       // EPI_PUPD
+    void *x;             // EPI_PUPD: iterate that takes the pending alpha p_old (NULL: none)
     void *pbuf[2];       // EPI_PUPD, and EPI_PLAIN / EPI_NORMAL when psel
     int psel;            // EPI_PLAIN: in = p_new; EPI_NORMAL: q = p_new
     int reverse;         // visit the sites from the last index down (the second Dslash of a CG
@@ -111,20 +112,24 @@ struct MrhsArgs {
 
 qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t st);
 
-// x += alpha p_new; r -= alpha ap; ||r||^2 -> S (rr, beta, flags); sets the
-// graph conditions when ctl.active.
+// x += alpha p_new (x NULL: left to the next iteration's first Dslash);
+// r -= alpha ap; ||r||^2 -> S (rr, beta, flags); sets the graph conditions
+// when ctl.active.
 qex_status launch_update_xr(qex_lattice *lat, qex_prec prec, void *x, void *r, void *const pbuf[2],
                             const void *ap, CgScalars *S, const GraphCtl &ctl, cudaStream_t st);
 // p_new = r + beta p_old with the buffers chosen by the iteration parity
 // (halt-checked); the FP64 iteration's first kernel.
 qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void *const pbuf[2], CgScalars *S,
                            cudaStream_t st);
-// x64 += (double) xh32; xh32 = 0.
-qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, cudaStream_t st);
-// r32 = (float) r64 (r32 may be NULL: only the graph condition is set);
-// loop condition = !halt when ctl.active.
-qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, const CgScalars *S,
-                            const GraphCtl &ctl, cudaStream_t st);
+// x64 += (double) xh32 + alpha p with p = pbuf[iters & 1] (the update the
+// iteration left pending; pbuf NULL: none); xh32 = 0.
+qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, float *const pbuf[2], const CgScalars *S,
+                          cudaStream_t st);
+// r32 = (float) r64 (r32 may be NULL: only the graph condition is set),
+// alpha = 0 (no pending iterate update after a reliable update); loop
+// condition = !halt when ctl.active.
+qex_status launch_finish_ru(qex_lattice *lat, const double *r64, float *r32, CgScalars *S, const GraphCtl &ctl,
+                            cudaStream_t st);
 // *flag |= (some element of the FP64 half field f is not zero; NaN counts).
 qex_status launch_any_nonzero(qex_lattice *lat, const double *f, int *flag, cudaStream_t st);
 // ||f||^2 -> *out (FP64, fixed order); if S, also S->bb and S->stop2.
