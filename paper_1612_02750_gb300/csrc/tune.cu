@@ -11,8 +11,8 @@
 //   * the plain Dslash with 256, 128 and 64 threads per block,
 //   * the normal-operator Dslash (grid reduction) with a few (block, blocks
 //     per SM) pairs, the persistent grid and one thread per site among them,
-//   * optionally the CG vector update with its grid capped at 2, 4, 8 or 16
-//     blocks per SM,
+//   * optionally the CG vector update (in the form the solve runs) with its
+//     grid capped at 2, 4, 8 or 16 blocks per SM,
 // and keeps a candidate only if it beats the compiled default by more than
 // 2 %.  Results are cached per process, keyed by (SM count, extents,
 // boundary, precision, Naik), and in the text file named by QEX_TUNE_CACHE
@@ -217,7 +217,10 @@ qex_status measure(qex_lattice *lat, qex_prec prec, const void *fat, const void 
         if (s) break;
         cur = best.shape;
         if (tune_blas) {
-            // the CG vector update (x += alpha p, r -= alpha A p, ||r||^2) in prec
+            // the CG vector update in prec, in the form the solve runs: FP64
+            // x += alpha p, r -= alpha A p, ||r||^2; FP32 without the iterate
+            // (the mixed solve folds it into the next iteration's Dslash)
+            void *const xu = prec == QEX_F64 ? f0 : nullptr;
             const int caps[4] = {QEX_BLAS_BLOCKS_PER_SM > 0 ? QEX_BLAS_BLOCKS_PER_SM : 4, 2, 8, 16};
             void *pb[2] = {f2, f2};
             const GraphCtl off = {};
@@ -226,7 +229,7 @@ qex_status measure(qex_lattice *lat, qex_prec prec, const void *fat, const void 
                 lat->blas_per_sm = caps[k];
                 reset_S();
                 float t = 0.f;
-                s = time_us([&] { return launch_update_xr(lat, prec, f0, f1, pb, f2, S, off, st); }, st, &t);
+                s = time_us([&] { return launch_update_xr(lat, prec, xu, f1, pb, f2, S, off, st); }, st, &t);
                 if (!s && (k == 0 || t < 0.98f * t_best)) {
                     t_best = t;
                     best.blas_per_sm = caps[k];
