@@ -381,7 +381,8 @@ qex_status qex_tune(const qex_lattice *lat, qex_prec prec, const void *fat, cons
  * persistent grid in blocks per SM (0: one thread per site), out[3] the
  * vector kernels' grid cap in blocks per SM, out[4] where they came from (0
  * compiled defaults, not tuned yet; 1 measured; 2 cache; 3 defaults kept by
- * QEX_TUNE=0).  out is a host array of 5 ints.  Errors: QEX_ERR_ARG. */
+ * QEX_TUNE=0), out[5] the non-reducing Dslash grid cap in resident waves (0:
+ * one thread per site).  out is a host array of 6 ints.  Errors: QEX_ERR_ARG. */
 qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int naik, int *out);
 
 /* Number of kernels this library has launched in the calling process so far

@@ -462,11 +462,11 @@ def qex_tune(lat: Lattice, prec, fat, lng=None, stream=None):
 
 def qex_tune_info(lat: Lattice, prec, naik: bool = False) -> dict:
     """Launch shapes in use for (lat, prec, naik)."""
-    out = (ctypes.c_int * 5)()
+    out = (ctypes.c_int * 6)()
     _check(load().qex_tune_info(lat.handle, _prec(prec), 1 if naik else 0, out))
     src = {0: "default", 1: "measured", 2: "cache", 3: "disabled"}
     return {"dslash_block": out[0], "reduce_block": out[1], "reduce_blocks_per_sm": out[2],
-            "blas_blocks_per_sm": out[3], "source": src.get(out[4], str(out[4]))}
+            "blas_blocks_per_sm": out[3], "source": src.get(out[4], str(out[4])), "dslash_waves": out[5]}
 
 
 def qex_launch_count() -> int:

@@ -194,7 +194,10 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
 // end in a grid reduction, a persistent grid of as many blocks per SM as the
 // launch bounds keep resident, so that each block pays the reduction's
 // fence-and-atomic tail once.  The autotuner may replace the block size and
-// the persistent grid per (precision, Naik) of the lattice.
+// the persistent grid per (precision, Naik) of the lattice, and may cap the
+// other variants' grid at a few resident waves (min_blocks x kDslashBlock
+// threads per SM each), each thread then taking ~1-2 sites grid-stride: on a
+// launch of 3-4 waves this trims the partial last wave.
 static void dslash_shape(const qex_lattice *lat, qex_prec prec, bool naik, bool reducing, int min_blocks, int *grid,
                          int *block) {
     const LaunchShape &sh = lat->shape[prec][naik ? 1 : 0];
@@ -210,6 +213,10 @@ static void dslash_shape(const qex_lattice *lat, qex_prec prec, bool naik, bool 
     if (reducing && per_sm > 0) {
         const int persistent = sm_count() * per_sm;
         if (persistent < full) *grid = persistent;
+    }
+    if (!reducing && sh.red_block > 0 && sh.ds_waves > 0) {
+        const int capped = sm_count() * sh.ds_waves * (min_blocks * kDslashBlock / b);
+        if (capped > 0 && capped < full) *grid = capped;
     }
 }
 

@@ -500,6 +500,8 @@ struct LaunchShape {
     int ds_block;    // threads per block of the non-reducing Dslash variants
     int red_block;   // threads per block of the reducing variants (0: defaults for both fields)
     int red_per_sm;  // their persistent grid, blocks per SM (0: one thread per site)
+    int ds_waves;    // non-reducing grid capped at this many resident waves, sites
+                     // taken grid-stride (0: one thread per site)
 };
 
 }  // namespace qex

@@ -8,7 +8,9 @@
 // variants want a persistent grid whose per-block reduction tail is paid once)
 // and is measured, not guessed: for one (precision, Naik) of a lattice the
 // tuner times, with CUDA events on scratch fields,
-//   * the plain Dslash with 256, 128 and 64 threads per block,
+//   * the plain Dslash with 256, 128 and 64 threads per block, each with one
+//     thread per site and with the grid capped at two resident waves (when
+//     that is fewer blocks),
 //   * the normal-operator Dslash (grid reduction) with a few (block, blocks
 //     per SM) pairs, the persistent grid and one thread per site among them,
 //   * optionally the CG vector update (in the form the solve runs) with its
@@ -53,7 +55,7 @@ std::string key_of(const qex_lattice *lat, qex_prec prec, int naik) {
     return buf;
 }
 
-// "qex-tune-v1 <key with spaces> | ds red per_sm blas"
+// "qex-tune-v1 <key with spaces> | ds red per_sm blas [ds_waves]"
 void load_file_locked() {
     if (g_file_loaded) return;
     g_file_loaded = true;
@@ -68,13 +70,13 @@ void load_file_locked() {
         if (!bar) continue;
         TuneRecord r;
         memset(&r, 0, sizeof(r));
-        if (sscanf(bar + 1, "%d %d %d %d", &r.shape.ds_block, &r.shape.red_block, &r.shape.red_per_sm,
-                   &r.blas_per_sm) != 4)
+        if (sscanf(bar + 1, "%d %d %d %d %d", &r.shape.ds_block, &r.shape.red_block, &r.shape.red_per_sm,
+                   &r.blas_per_sm, &r.shape.ds_waves) < 4)
             continue;
         const bool ok_block = [](int b) { return b == 64 || b == 128 || b == 256; }(r.shape.ds_block) &&
                               (r.shape.red_block == 64 || r.shape.red_block == 128 || r.shape.red_block == 256);
         if (!ok_block || r.shape.red_per_sm < 0 || r.shape.red_per_sm > 16 || r.blas_per_sm < 0 ||
-            r.blas_per_sm > 16)
+            r.blas_per_sm > 16 || r.shape.ds_waves < 0 || r.shape.ds_waves > 8)
             continue;
         std::string key(line + 12, bar - (line + 12));
         while (!key.empty() && key.back() == ' ') key.pop_back();
@@ -88,8 +90,8 @@ void append_file_locked(const std::string &key, const TuneRecord &r) {
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "qex-tune-v1 %s | %d %d %d %d\n", key.c_str(), r.shape.ds_block, r.shape.red_block,
-            r.shape.red_per_sm, r.blas_per_sm);
+    fprintf(f, "qex-tune-v1 %s | %d %d %d %d %d\n", key.c_str(), r.shape.ds_block, r.shape.red_block,
+            r.shape.red_per_sm, r.blas_per_sm, r.shape.ds_waves);
     fclose(f);
 }
 
@@ -98,24 +100,24 @@ bool tuning_enabled() {
     return !(e && strcmp(e, "0") == 0);
 }
 
-// Average time of one launch, in microseconds: two warm-up launches, then
-// enough to cover about half a millisecond (3 to 50).
+// Time of one launch, in microseconds: two warm-up launches and a short
+// calibration batch, then the least per-launch average of three batches of
+// about half a millisecond each (3 to 50 launches; the minimum keeps a
+// candidate's number from a batch that another process on the GPU slowed).
 template <typename F>
 qex_status time_us(F launch, cudaStream_t st, float *us) {
     cudaEvent_t a, b;
     QEX_CUDA(cudaEventCreate(&a));
     QEX_CUDA(cudaEventCreate(&b));
     qex_status s = QEX_OK;
-    float ms = 0.f;
+    float ms = 0.f, best = 0.f;
     int reps = 3;
-    for (int pass = 0; pass < 2 && !s; ++pass) {
-        if (pass == 0) {
-            for (int k = 0; k < 2 && !s; ++k) s = launch();
-        }
-        if (s) break;
+    for (int k = 0; k < 2 && !s; ++k) s = launch();
+    for (int pass = 0; pass < 4 && !s; ++pass) {
         cudaEventRecord(a, st);
         for (int k = 0; k < reps && !s; ++k) s = launch();
         cudaEventRecord(b, st);
+        if (s) break;
         if (cudaEventSynchronize(b) != cudaSuccess) {
             s = cuda_fail(cudaGetLastError(), "timing a launch shape");
             break;
@@ -125,10 +127,11 @@ qex_status time_us(F launch, cudaStream_t st, float *us) {
         if (pass == 0) {
             int want = per > 0.f ? (int)(500.f / per) : 50;
             reps = want < 3 ? 3 : (want > 50 ? 50 : want);
-        } else {
-            *us = per;
+        } else if (pass == 1 || per < best) {
+            best = per;
         }
     }
+    if (!s) *us = best;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return s;
@@ -174,7 +177,7 @@ qex_status measure(qex_lattice *lat, qex_prec prec, const void *fat, const void 
     a.c3 = lng ? -1.0 / 24.0 : 0.0;
     a.m2 = 0.01;
     do {
-        // plain Dslash: block size
+        // plain Dslash: block size, one thread per site or two resident waves
         a.epi = EPI_PLAIN;
         a.out_parity = 1;
         a.in = f0;
@@ -182,15 +185,21 @@ qex_status measure(qex_lattice *lat, qex_prec prec, const void *fat, const void 
         a.S = nullptr;
         float t_best = 0.f;
         const int blocks[3] = {256, 128, 64};
-        for (int k = 0; k < 3 && !s; ++k) {
-            cur.ds_block = blocks[k];
+        for (int k = 0; k < 6 && !s; ++k) {
+            const int blk = blocks[k % 3], waves = k < 3 ? 0 : 2;
+            // a cap that does not cut the grid is the uncapped launch again
+            if (waves && (long long)sm_count() * waves * (minb * kDslashBlock / blk) >= blocks_for(lat->vh, blk))
+                continue;
+            cur.ds_block = blk;
+            cur.ds_waves = waves;
             cur.red_block = kDslashBlock;
             cur.red_per_sm = def_per_sm;
             float t = 0.f;
             s = time_us([&] { return launch_dslash(lat, a, st); }, st, &t);
             if (!s && (k == 0 || t < 0.98f * t_best)) {
                 t_best = t;
-                best.shape.ds_block = blocks[k];
+                best.shape.ds_block = blk;
+                best.shape.ds_waves = waves;
             }
         }
         if (s) break;
@@ -204,6 +213,7 @@ qex_status measure(qex_lattice *lat, qex_prec prec, const void *fat, const void 
         const int cand[5][2] = {{256, def_per_sm}, {256, 0}, {128, 2 * minb}, {128, minb}, {64, 4 * minb}};
         for (int k = 0; k < 5 && !s; ++k) {
             cur.ds_block = best.shape.ds_block;
+            cur.ds_waves = best.shape.ds_waves;
             cur.red_block = cand[k][0];
             cur.red_per_sm = cand[k][1];
             float t = 0.f;
@@ -349,5 +359,6 @@ extern "C" qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int n
     out[2] = set ? sh.red_per_sm : (QEX_REDUCE_BLOCKS_PER_SM >= 0 ? QEX_REDUCE_BLOCKS_PER_SM : minb);
     out[3] = lat->blas_per_sm > 0 ? lat->blas_per_sm : QEX_BLAS_BLOCKS_PER_SM;
     out[4] = lat->tuned[prec][naik ? 1 : 0];
+    out[5] = set ? sh.ds_waves : 0;
     return QEX_OK;
 }

@@ -66,6 +66,7 @@ def test_tuned_shapes_keep_dslash_bits(q, monkeypatch, dims, prec, naik):
     assert info["source"] == "measured", info
     assert info["dslash_block"] in (64, 128, 256) and info["reduce_block"] in (64, 128, 256)
     assert 0 <= info["reduce_blocks_per_sm"] <= 16 and info["blas_blocks_per_sm"] in (2, 4, 8, 16)
+    assert info["dslash_waves"] in (0, 2)
     got = q.qex_dslash(lat, prec, fat, lng, C3, 1, inp)
     got_n = q.qex_normal_op(lat, prec, fat, lng, C3, 0.1, inp)
     assert torch.equal(got, ref) and torch.equal(got_n, ref_n)
@@ -125,10 +126,57 @@ def test_tune_cache_file_round_trip(q, tmp_path):
         assert r.returncode == 0, r.stderr[-2000:]
         runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
     assert runs[0]["source"] == "measured" and runs[1]["source"] == "cache"
-    for k in ("dslash_block", "reduce_block", "reduce_blocks_per_sm"):
+    for k in ("dslash_block", "reduce_block", "reduce_blocks_per_sm", "dslash_waves"):
         assert runs[0][k] == runs[1][k]
     lines = [ln for ln in path.read_text().splitlines() if ln.startswith("qex-tune-v1 ")]
     assert len(lines) == 1 and "dims8x8x8x8" in lines[0] and "prec1 naik0" in lines[0]
+    assert len(lines[0].split("|")[1].split()) == 5
+
+
+CAPPED = r"""
+import hashlib, json, sys
+import torch
+import paper_1612_02750_gb300 as q
+q.load()
+torch.manual_seed(5)
+lat = q.Lattice((32, 32, 32, 32))
+fat64 = q.empty_links(lat, "f64").normal_()
+fat32 = q.qex_convert_links(lat, "f64", fat64, "f32")
+fat16 = q.qex_convert_links(lat, "f64", fat64, "f32r12h")
+inp = q.empty_field(lat, "f32r12h").normal_()
+out = q.qex_dslash(lat, "f32r12h", fat16, None, 0.0, 1, inp)
+b = q.empty_field(lat, "f64").normal_()
+x = torch.zeros_like(b)
+st, stats = q.qex_cg(lat, "f32", fat64, None, fat32, None, 0.0, 0.5, b, x, tol=1e-10, delta=0.1)
+h = lambda t: hashlib.sha1(t.cpu().numpy().tobytes()).hexdigest()
+print(json.dumps({"dslash": h(out), "x": h(x), "iters": stats["iters"], "status": st,
+                  "waves": [q.qex_tune_info(lat, p)["dslash_waves"] for p in ("f32r12h", "f32")]}))
+"""
+
+
+def test_capped_grid_keeps_bits(q, tmp_path):
+    """On 32^4 (a launch of ~3.4 resident waves) the plain Dslash and the
+    mixed solve give the same bits with one thread per site and with the grid
+    capped at two resident waves (sites taken grid-stride)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    runs = []
+    for waves in (0, 2):
+        path = tmp_path / f"tune_{waves}.txt"
+        path.write_text("".join(f"qex-tune-v1 sm{sms} dims32x32x32x32 ap1 prec{p} naik0 | 128 256 4 0 {w}\n"
+                                for p, w in ((0, 0), (1, waves), (3, waves))))
+        env = dict(os.environ, QEX_TUNE_CACHE=str(path), PYTHONPATH=ROOT)
+        env.pop("QEX_TUNE", None)
+        env.pop("QEX_CG_MODE", None)
+        r = subprocess.run([sys.executable, "-c", CAPPED], env=env, cwd=ROOT, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert runs[0]["waves"] == [0, 0] and runs[1]["waves"] == [2, 2]
+    assert runs[0]["status"] == 0 and runs[0]["iters"] > 0
+    for k in ("dslash", "x", "iters", "status"):
+        assert runs[0][k] == runs[1][k], k
 
 
 def test_tune_errors(q):
