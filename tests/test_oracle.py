@@ -8,6 +8,8 @@ linear algebra on tiny lattices.  Each test says which plausible mistake it
 catches.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -146,23 +148,25 @@ def test_gauge_covariance(oracle_mod, naik):
         assert np.linalg.norm(d2 - expect) <= 1e-13 * np.linalg.norm(expect)
 
 
-# Hand-derived: unit links, 8^4, antiperiodic time, point source of colour 2 at
-# x0 = (1,0,0,0).  (D psi)(x0 - mu) = +eta_mu(x0) b, (D psi)(x0 + mu) =
-# -eta_mu(x0) b, with eta(x0) = (1, -1, -1, -1) for mu = x, y, z, t; the link
-# from t = 7 to t = 0 carries b = -1.  Naik: (x0 - 3mu) gets +c3 eta b and
-# (x0 + 3mu) gets -c3 eta b; the long link leaving t = 5 crosses the boundary.
-POINT_ONE_HOP = {
-    (0, 0, 0, 0): +1, (2, 0, 0, 0): -1,
-    (1, 7, 0, 0): -1, (1, 1, 0, 0): +1,
-    (1, 0, 7, 0): -1, (1, 0, 1, 0): +1,
-    (1, 0, 0, 7): +1, (1, 0, 0, 1): +1,
-}
-POINT_THREE_HOP = {
-    (6, 0, 0, 0): +1, (4, 0, 0, 0): -1,
-    (1, 5, 0, 0): -1, (1, 3, 0, 0): +1,
-    (1, 0, 5, 0): -1, (1, 0, 3, 0): +1,
-    (1, 0, 0, 5): +1, (1, 0, 0, 3): +1,
-}
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_point_source_golden():
+    """Hand-derived D psi for a point source on unit links (8^4, antiperiodic
+    time, colour 2 at (1,0,0,0)): {"one": {(x,y,z,t): v}, "three": {...}}."""
+    out = {"one": {}, "three": {}}
+    with open(os.path.join(GOLDEN, "point_source_unit_links_8x8x8x8.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            x, y, z, t = (int(v) for v in line[:4])
+            out[line[4]][(x, y, z, t)] = int(line[5])
+    return out
+
+
+POINT = read_point_source_golden()
+POINT_ONE_HOP, POINT_THREE_HOP = POINT["one"], POINT["three"]
 
 
 @pytest.mark.parametrize("naik", [False, True])
@@ -170,6 +174,7 @@ def test_point_source_hand_values(oracle_mod, naik):
     """Fixes the conventions the invariants leave open: the eta ordering
     (x, y, z, t with eta_mu from the coordinates before mu), the sign of the
     forward term and the link that carries the antiperiodic sign."""
+    assert len(POINT_ONE_HOP) == 8 and len(POINT_THREE_HOP) == 8  # one entry per hop direction
     dims = (8, 8, 8, 8)
     u = fg.unit_links(dims)
     psi = np.zeros(fg.lattice_shape(dims) + (3,), dtype=np.complex128)
