@@ -28,18 +28,21 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (OpenMP site loops, no FMA contraction)."""
-    src = os.path.join(_HERE, "qex_oracle.c")
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
-        return _SO
-    os.makedirs(_BUILD, exist_ok=True)
-    tmp = _SO + f".{os.getpid()}.tmp"
+def build(force: bool = False, src: str | None = None, out: str | None = None) -> str:
+    """Compile the C oracle with gcc (OpenMP site loops, no FMA contraction).
+    ``src``/``out`` compile another copy of the source with the same flags
+    (the pin tests build deliberately broken copies this way)."""
+    src = src or os.path.join(_HERE, "qex_oracle.c")
+    so = out or _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(src):
+        return so
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    tmp = so + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
            "-fcx-limited-range", src, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
 def _load():
