@@ -358,7 +358,9 @@ qex_status qex_cg_host(const qex_lattice *lat, qex_prec inner, const double *hos
  * CG vector kernels.  The paper has no counterpart: this is a GPU launch-
  * configuration search.  For (lat, prec, Naik iff lng != NULL) qex_tune times,
  * with CUDA events on scratch fields it allocates and frees (about three half
- * fields), the plain Dslash at 256, 128 and 64 threads per block, the
+ * fields), the plain Dslash at 256, 128 and 64 threads per block (one thread
+ * per site, and a grid capped at two resident waves with the sites taken
+ * grid-stride where that cap cuts the grid), the
  * normal-operator Dslash (which ends in a grid reduction) at a few block
  * sizes and grids, and the CG vector update with its grid capped at 2, 4, 8
  * or 16 blocks per SM; it keeps a shape only if it beats the compiled default
