@@ -116,6 +116,35 @@ def test_pack_roundtrip_bit_exact(q, dims):
     assert np.array_equal(host(q.qex_unpack_links(lat, "f64", l64)), u.astype(np.complex64).astype(np.complex128))
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 10)])
+def test_convert_field_bit_exact(q, dims):
+    """Half fields: F64 -> F32 rounds each real to nearest (numpy's cast),
+    F32 -> F64 is exact, a conversion within FP64 or within the FP32-class
+    formats (all of which keep FP32 vectors) copies; a NULL input is an
+    argument error."""
+    import torch
+
+    s = fg.rng_streams(43)
+    f = fg.gaussian_field(s["source"], dims)
+    lat = q.Lattice(dims)
+    ev = fg.even_mask(dims)
+    rounded = f.astype(np.complex64).astype(np.complex128)
+    for p in (0, 1):
+        mine = ev if p == 0 else ~ev
+        h64 = q.qex_pack_field(lat, "f64", p, dev(f))
+        h32 = q.qex_convert_field(lat, "f64", h64, "f32")
+        assert np.array_equal(host(q.qex_unpack_field(lat, "f32", p, h32))[mine], rounded[mine])
+        assert torch.equal(h32, q.qex_pack_field(lat, "f32", p, dev(f)))
+        back = q.qex_convert_field(lat, "f32", h32, "f64")
+        assert np.array_equal(host(q.qex_unpack_field(lat, "f64", p, back))[mine], rounded[mine])
+        assert torch.equal(q.qex_convert_field(lat, "f64", h64, "f64"), h64)
+        for fmt in ("f32r12", "f32r12h", "f32s16"):
+            assert torch.equal(q.qex_convert_field(lat, "f32", h32, fmt), h32)
+    with pytest.raises(q.QexError) as e:
+        q.qex_convert_field(lat, "f64", None, "f32")
+    assert e.value.status == 1
+
+
 @pytest.mark.parametrize("kind", ["haar", "exp"])
 def test_two_row_links_roundtrip(q, kind):
     """SU(3) links stored as two FP32 rows come back with the third row rebuilt
