@@ -58,6 +58,27 @@ def _lattice(lib, dims, ap=1):
     return st, h
 
 
+def test_volume_and_version_host_calls(lib):
+    """qex_volume / qex_half_volume of a lattice (-1 for NULL), the same
+    through the binding, and a non-empty version string; none touches the
+    device."""
+    import paper_1612_02750_gb300 as q
+
+    for dims in [(4, 4, 4, 4), (6, 4, 2, 8), (64, 64, 64, 64)]:
+        st, h = _lattice(lib, dims)
+        assert st == 0
+        try:
+            V = int(np.prod(dims))
+            assert lib.qex_volume(h) == V and lib.qex_half_volume(h) == V // 2
+        finally:
+            lib.qex_lattice_destroy(h)
+        lat = q.Lattice(dims)
+        assert (lat.volume, lat.half_volume) == (int(np.prod(dims)), int(np.prod(dims)) // 2)
+    assert lib.qex_volume(None) == -1 and lib.qex_half_volume(None) == -1
+    v = q.qex_version()
+    assert v and v.isprintable()
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (2, 6, 4, 10), (8, 4, 6, 4)])
 def test_host_index_math_matches_oracle(lib, oracle_mod, dims):
     st, h = _lattice(lib, dims)
