@@ -50,7 +50,8 @@ __device__ __forceinline__ void set_conditions(const GraphCtl &ctl, unsigned int
     }
 }
 
-// x += alpha p_new; r -= alpha ap; ||r||^2 -> rr_new; then the CG scalar
+// x += alpha p_new (DO_X; otherwise the next iteration's first Dslash adds
+// it); r -= alpha ap; ||r||^2 -> rr_new; then the CG scalar
 // logic: continue (beta = rr_new / rr), or ask for a reliable update
 // (iterated residual small enough, or the iteration cap reached), or stop
 // on a NaN.  In the graph solve the last block also sets the loop and
