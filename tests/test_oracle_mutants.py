@@ -11,7 +11,9 @@ make: a transposed instead of adjoint link, the wrong eta ordering, a boundary
 sign on one hop direction or on the wrong three-hop links, the backward link
 read at the wrong site, the sign of the normal operator, a rescaled Naik term,
 the CG coefficients, and the force's parity sign, field roles, trace term,
-conjugation and Naik coefficient.
+conjugation and Naik coefficient.  Two more are planted in the marshalling
+module's pseudofermion phi = (M^+ chi)_e: the hopping term with the wrong sign
+and m^2 in place of m.
 """
 
 import importlib.util
@@ -24,6 +26,7 @@ import test_oracle_force as F
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "qex_oracle.c")
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
 
 # name -> (text in qex_oracle.c, replacement, occurrences, pin that must fail)
 MUTANTS = {
@@ -55,6 +58,12 @@ MUTANTS = {
                                     "force_links(L, antiperiodic, W, 1.0, 3, X, Y, kind, out_long);", 1, "force_fd"),
 }
 
+# the same, planted in the marshalling module (the C source is left intact)
+PY_MUTANTS = {
+    "pseudofermion_hop_sign": ("phi = mass * chi - dch", "phi = mass * chi + dch", 1, "pseudofermion"),
+    "pseudofermion_mass_squared": ("phi = mass * chi - dch", "phi = mass * mass * chi - dch", 1, "pseudofermion"),
+}
+
 
 def _runs(*calls):
     def run(m):
@@ -84,6 +93,8 @@ PINS = {
                       F.test_gradient_form_matches_finite_differences),
     "force_traceless": _runs(F.test_force_is_traceless_antihermitian_and_relates_to_gradient),
     "force_gauge": _runs(F.test_force_gauge_covariance),
+    "pseudofermion": _runs(*[lambda m, d=d, n=n: F.test_pseudofermion_is_mdagger_chi_on_even_sites(m, d, n)
+                             for d, n in (((2, 2, 2, 2), False), ((4, 2, 2, 4), True))]),
 }
 
 
@@ -97,13 +108,20 @@ def _failing_pins(module):
     return failed
 
 
-def _load_copy(tmp_path, name, text):
+def _load_copy(tmp_path, name, text, py_text=None):
+    """Build the C text with the oracle's flags and load it through a fresh
+    instance of the marshalling module (``py_text``: a modified copy of it)."""
     src = tmp_path / f"{name}.c"
     src.write_text(text)
     import oracle
 
     so = oracle.build(force=True, src=str(src), out=str(tmp_path / f"lib{name}.so"))
-    spec = importlib.util.spec_from_file_location(f"oracle_copy_{name}", os.path.join(ROOT, "oracle", "__init__.py"))
+    py = PY_SRC
+    if py_text is not None:
+        py = str(tmp_path / f"oracle_{name}.py")
+        with open(py, "w") as f:
+            f.write(py_text)
+    spec = importlib.util.spec_from_file_location(f"oracle_copy_{name}", py)
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     mod.build = lambda force=False, src=None, out=None: so  # load this copy, never rebuild it
@@ -126,5 +144,18 @@ def test_planted_mistake_fails_a_pin(tmp_path, name):
         text = f.read()
     assert text.count(old) == count, f"mutation site of {name} not found in the oracle source"
     mod = _load_copy(tmp_path, name, text.replace(old, new))
+    with pytest.raises(Exception):
+        PINS[pin](mod)
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_planted_mistake_in_marshalling_fails_a_pin(tmp_path, name):
+    old, new, count, pin = PY_MUTANTS[name]
+    with open(SRC) as f:
+        text = f.read()
+    with open(PY_SRC) as f:
+        py_text = f.read()
+    assert py_text.count(old) == count, f"mutation site of {name} not found in the marshalling module"
+    mod = _load_copy(tmp_path, name, text, py_text.replace(old, new))
     with pytest.raises(Exception):
         PINS[pin](mod)
