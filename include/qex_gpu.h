@@ -110,63 +110,94 @@ typedef struct {
 
 /* Create a lattice of extents dims[4] = {Lx,Ly,Lz,Lt}; antiperiodic_t != 0
  * makes time antiperiodic for fermions.  Errors: QEX_ERR_ARG (null),
- * QEX_ERR_SHAPE (odd extent, extent < 2, V >= 2^31). */
+ * QEX_ERR_SHAPE (odd extent, extent < 2, V >= 2^31).
+ * Paper: Sec. 4 (the lattice the staggered operator acts on; Fig. 1 runs the
+ * solver on L^3 x T volumes).  Boundary condition and size limits are this
+ * library's.
+ */
 qex_status qex_lattice_create(const int dims[4], int antiperiodic_t, qex_lattice **out);
 
 /* Free the lattice and all scratch it owns (synchronises the device first).
- * NULL is accepted. */
+ * NULL is accepted.
+ * Paper: no counterpart (resource management of this library).
+ */
 qex_status qex_lattice_destroy(qex_lattice *lat);
 
-/* Volume V and half volume Vh. */
+/* Volume V and half volume Vh.
+ * Paper: no counterpart.
+ */
 int64_t qex_volume(const qex_lattice *lat);
 int64_t qex_half_volume(const qex_lattice *lat);
 
 /* Even-odd index parity*Vh + (lex >> 1) of coord[4] = {x,y,z,t}
- * (host function; -1 on bad arguments). */
+ * (host function; -1 on bad arguments).
+ * Paper: no counterpart (the even-odd site order is this library's layout; the
+ * paper describes QEX's data layout only in general terms, Sec. 3).
+ */
 int64_t qex_eo_index(const qex_lattice *lat, const int coord[4]);
 
 /* Neighbour table: for the i-th site x of parity `parity` (i in [0,Vh)),
  * host_out[i] = index, within the opposite parity, of x + hop*mu_hat
  * (periodic wrap), hop in {+1,-1,+3,-3}.  Computed on the host with the same
- * index arithmetic the kernels use.  host_out holds Vh int32. */
+ * index arithmetic the kernels use.  host_out holds Vh int32.
+ * Paper: Sec. 4 names the operator whose hops these are (x +- mu, and x +- 3mu
+ * for the Naik term); the table itself has no counterpart.
+ */
 qex_status qex_neighbor_table(const qex_lattice *lat, int parity, int mu, int hop, int32_t *host_out);
 
-/* Same table written by a kernel into device memory dev_out (Vh int32). */
+/* Same table written by a kernel into device memory dev_out (Vh int32).
+ * Paper: as qex_neighbor_table.
+ */
 qex_status qex_neighbor_table_device(const qex_lattice *lat, int parity, int mu, int hop,
                                      int32_t *dev_out, void *stream);
 
 /* ---------------------------------------------------------------- layout */
 
-/* Bytes of one internal link set (4V links) and of one internal half field. */
+/* Bytes of one internal link set (4V links) and of one internal half field.
+ * Paper: no counterpart (layout of this library).
+ */
 size_t qex_links_bytes(const qex_lattice *lat, qex_prec prec);
 size_t qex_field_bytes(const qex_lattice *lat, qex_prec prec);
 
 /* Format of the long (Naik) link set that an operator of precision prec
- * reads (see the precisions above); -1 for an unknown prec. */
+ * reads (see the precisions above); -1 for an unknown prec.
+ * Paper: no counterpart (link formats of this library).
+ */
 int qex_long_links_prec(qex_prec prec);
 
 /* Canonical lex links (complex double, [V][4][3][3]) -> internal links of
  * precision prec (F32 rounds to nearest).  lex_links and internal must not
- * overlap. */
+ * overlap.
+ * Paper: no counterpart (layout conversion).
+ */
 qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *lex_links,
                           void *internal, void *stream);
 
-/* Internal links -> canonical lex links (complex double). */
+/* Internal links -> canonical lex links (complex double).
+ * Paper: no counterpart (layout conversion).
+ */
 qex_status qex_unpack_links(const qex_lattice *lat, qex_prec prec, const void *internal,
                             double *lex_links, void *stream);
 
 /* Sites of parity `parity` of a canonical full-lattice field ([V][3] complex
- * double) -> internal half field of precision prec. */
+ * double) -> internal half field of precision prec.
+ * Paper: no counterpart (layout conversion).
+ */
 qex_status qex_pack_field(const qex_lattice *lat, qex_prec prec, int parity, const double *lex_field,
                           void *half, void *stream);
 
 /* Internal half field -> the parity-`parity` sites of a canonical field
- * (sites of the other parity are left untouched). */
+ * (sites of the other parity are left untouched).
+ * Paper: no counterpart (layout conversion).
+ */
 qex_status qex_unpack_field(const qex_lattice *lat, qex_prec prec, int parity, const void *half,
                             double *lex_field, void *stream);
 
 /* Precision conversion of internal links or half fields (F64 -> F32 rounds
- * to nearest, F32 -> F64 is exact).  in and out must not overlap. */
+ * to nearest, F32 -> F64 is exact).  in and out must not overlap.
+ * Paper: Sec. 4 runs the solver in single and double precision; the
+ * conversions between this library's formats have no counterpart.
+ */
 qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to,
                              void *out, void *stream);
 qex_status qex_convert_field(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to,
@@ -178,7 +209,11 @@ qex_status qex_convert_field(const qex_lattice *lat, qex_prec from, const void *
  * parity-(1-p) half field `in` to the parity-p half field `out`.  fat: one
  * internal link set (U); lng: long links W for the Naik term, or NULL;
  * c_naik: the Naik coefficient c3 (ignored when lng is NULL).  in, out, fat,
- * lng share precision prec.  in and out must not overlap. */
+ * lng share precision prec.  in and out must not overlap.
+ * Paper: Sec. 4 (the Dirac operator of the staggered fermion action with the
+ * Naik term); the paper prints no formula, the one implemented is written out
+ * at the top of this header.
+ */
 qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                       double c_naik, int out_parity, const void *in, void *out, void *stream);
 
@@ -190,12 +225,18 @@ qex_status qex_dslash(const qex_lattice *lat, qex_prec prec, const void *fat, co
  * right-hand side, Fig. 1; batching them cuts the link traffic per vector by
  * nrhs).  `in` and `out` hold nrhs half fields back to back (field r starts
  * at r * qex_field_bytes(lat, prec)); they must not overlap.  1 <= nrhs <=
- * QEX_MRHS_MAX.  Other arguments and errors as qex_dslash. */
+ * QEX_MRHS_MAX.  Other arguments and errors as qex_dslash.
+ * Paper: Sec. 4 (the operator, as qex_dslash); several right-hand sides at once
+ * are this library's extension of the one-vector benchmark of Fig. 1.
+ */
 qex_status qex_dslash_mrhs(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                            double c_naik, int out_parity, int nrhs, const void *in, void *out, void *stream);
 
 /* out = (m^2 - D_eo D_oe) in on even sites; tmp_odd is a caller half field
- * (odd sites) that receives D_oe in. */
+ * (odd sites) that receives D_oe in.
+ * Paper: Sec. 4 and Fig. 1 (the matrix the conjugate-gradient solver inverts);
+ * the even-odd normal form m^2 - D_eo D_oe is this library's reading.
+ */
 qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                          double c_naik, double mass, const void *in, void *out, void *tmp_odd,
                          void *stream);
@@ -231,12 +272,16 @@ qex_status qex_normal_op_static(const qex_lattice *lat, qex_prec prec, const voi
                                 double c_naik, double mass, const void *in, void *out, void *stream);
 
 /* ||f||^2 of a half field, accumulated in FP64 in a fixed order
- * (bit-reproducible run to run); written to dev_out (one double, device). */
+ * (bit-reproducible run to run); written to dev_out (one double, device).
+ * Paper: Sec. 4 and Fig. 1 (the global sums of the conjugate-gradient solver).
+ */
 qex_status qex_norm2(const qex_lattice *lat, qex_prec prec, const void *f, double *dev_out,
                      void *stream);
 
 /* <a, b> = sum conj(a) b over a half field, FP64 accumulation, fixed order;
- * dev_out receives {re, im} (two doubles, device). */
+ * dev_out receives {re, im} (two doubles, device).
+ * Paper: Sec. 4 and Fig. 1 (the global sums of the conjugate-gradient solver).
+ */
 qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const void *b,
                    double *dev_out, void *stream);
 
@@ -264,7 +309,11 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  * iterate), QEX_ERR_NAN on a NaN/Inf or a non-positive <p, A p>,
  * QEX_ERR_TIMEOUT if a grid barrier of the persistent kernel waited longer
  * than about a second (blocks not co-resident; the kernel returns instead of
- * waiting forever). */
+ * waiting forever).
+ * Paper: Sec. 4 (single and double precision conjugate-gradient solvers of the
+ * staggered Dirac matrix) and Fig. 1 (one right-hand side); the mixed solve
+ * with FP64 reliable updates is this library's combination of the two.
+ */
 qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
                   const void *fat32, const void *lng32, double c_naik, double mass, const void *b64,
                   void *x64, double tol, int maxiter, double delta, void *stream,
@@ -301,7 +350,9 @@ qex_status qex_force(const qex_lattice *lat, const void *fat64, const void *lng6
  * meets tol; a reliable update requested by any running one is done for all
  * running ones.  stats (may be NULL) receives nrhs entries.  Synchronises the
  * stream.  Errors as qex_cg (QEX_ERR_NOT_CONVERGED if any right-hand side did
- * not converge). */
+ * not converge).
+ * Paper: extends the one-right-hand-side solver of Sec. 4 and Fig. 1.
+ */
 qex_status qex_cg_mrhs(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
                        const void *fat32, const void *lng32, double c_naik, double mass, int nrhs, const void *b64,
                        void *x64, double tol, int maxiter, double delta, void *stream, qex_cg_stats *stats);
@@ -335,7 +386,10 @@ typedef struct {
  * items[0].lat; the CG vectors of each item live in its own lattice's work
  * area.  stats (may be NULL) receives n entries.  Synchronises the stream.
  * Errors as qex_cg; QEX_ERR_ARG also for 0 or more than QEX_BATCH_MAX items,
- * items sharing a lattice object, or items disagreeing on the Naik term. */
+ * items sharing a lattice object, or items disagreeing on the Naik term.
+ * Paper: extends the solver of Sec. 4 and Fig. 1 (run there one L^3 x T volume
+ * at a time) to several lattices in one launch.
+ */
 qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inner, double tol, int maxiter, double delta,
                         void *stream, qex_cg_stats *stats);
 
@@ -348,7 +402,10 @@ qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inner, double 
  * [V][3]; its odd sites are set to zero).  Page-locked host buffers make the
  * copies asynchronous DMA.  Device staging (canonical and internal copies) is
  * owned by the lattice, allocated on first use and reused.  Synchronises the
- * stream.  Errors as qex_cg. */
+ * stream.  Errors as qex_cg.
+ * Paper: the solve of Sec. 4 and Fig. 1; the host-memory interface has no
+ * counterpart.
+ */
 qex_status qex_cg_host(const qex_lattice *lat, qex_prec inner, const double *host_fat, const double *host_lng,
                        double c_naik, double mass, const double *host_b, double *host_x, double tol, int maxiter,
                        double delta, void *stream, qex_cg_stats *stats);
@@ -384,17 +441,25 @@ qex_status qex_tune(const qex_lattice *lat, qex_prec prec, const void *fat, cons
  * vector kernels' grid cap in blocks per SM, out[4] where they came from (0
  * compiled defaults, not tuned yet; 1 measured; 2 cache; 3 defaults kept by
  * QEX_TUNE=0), out[5] the non-reducing Dslash grid cap in resident waves (0:
- * one thread per site).  out is a host array of 6 ints.  Errors: QEX_ERR_ARG. */
+ * one thread per site).  out is a host array of 6 ints.  Errors: QEX_ERR_ARG.
+ * Paper: no counterpart.
+ */
 qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int naik, int *out);
 
 /* Number of kernels this library has launched in the calling process so far
- * (monotone counter, for accounting of the kernels in a timed region). */
+ * (monotone counter, for accounting of the kernels in a timed region).
+ * Paper: no counterpart.
+ */
 uint64_t qex_launch_count(void);
 
-/* Message of the calling thread's last failed call ("" if none). */
+/* Message of the calling thread's last failed call ("" if none).
+ * Paper: no counterpart.
+ */
 const char *qex_last_error(void);
 
-/* Library version string. */
+/* Library version string.
+ * Paper: no counterpart.
+ */
 const char *qex_version(void);
 
 #ifdef __cplusplus

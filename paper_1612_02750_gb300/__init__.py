@@ -391,22 +391,29 @@ class StaggeredAction(torch.autograd.Function):
 
     forward(U, W, phi, lat, mass, c_naik, inner, tol, delta): phi is a
     canonical complex128 field whose even sites are the pseudofermion (held
-    fixed); inner = "f64" or a mixed precision ("f32", "f32r12").  The solve
-    is qex_cg; the backward pass is qex_dslash (Y = D_oe X) and qex_force
-    (kind 1), unpacked to canonical links: grad_U = 2 G^+ times the incoming
-    gradient (torch's convention for a real loss of complex inputs)."""
+    fixed); inner = "f64" or a mixed precision ("f32", "f32r12", "f32r12h",
+    "f32s16"; the two-row formats need SU(3) fat links).  The inner copies
+    are converted from the FP64 links: the fat links to ``inner``, the long
+    links to ``qex_long_links_prec(inner)``.  The solve is qex_cg; the
+    backward pass is qex_dslash (Y = D_oe X) and qex_force (kind 1),
+    unpacked to canonical links: grad_U = 2 G^+ times the incoming gradient
+    (torch's convention for a real loss of complex inputs)."""
 
     @staticmethod
     def forward(ctx, U, W, phi, lat, mass, c_naik=0.0, inner="f64", tol=1e-12, delta=0.01):
+        p = _prec(inner)  # raises ValueError for an unknown format
+        if p not in _NAMES:
+            raise ValueError(f"unknown inner precision {inner!r}")
         fat64 = qex_pack_links(lat, "f64", U.detach().contiguous())
         lng64 = qex_pack_links(lat, "f64", W.detach().contiguous()) if W is not None else None
         fat32 = lng32 = None
-        if _prec(inner) != F64:
-            fat32 = qex_convert_links(lat, "f64", fat64, inner)
-            lng32 = qex_convert_links(lat, "f64", lng64, "f32") if lng64 is not None else None
+        if p != F64:
+            fat32 = qex_convert_links(lat, "f64", fat64, p)
+            if lng64 is not None:
+                lng32 = qex_convert_links(lat, "f64", lng64, qex_long_links_prec(p))
         b = qex_pack_field(lat, "f64", 0, phi.detach().contiguous())
         x = torch.zeros_like(b)
-        qex_cg(lat, inner, fat64, lng64, fat32, lng32, c_naik, mass, b, x, tol=tol, delta=delta)
+        qex_cg(lat, p, fat64, lng64, fat32, lng32, c_naik, mass, b, x, tol=tol, delta=delta)
         s = qex_dot(lat, "f64", b, x)[0]
         ctx.lat, ctx.c_naik = lat, c_naik
         ctx.has_w = W is not None

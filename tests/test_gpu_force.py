@@ -186,3 +186,28 @@ def test_autograd_gradient(q, oracle_mod):
     S2.backward()
     assert S2.item() == pytest.approx(S_ref, rel=1e-9)
     assert relerr(U2.grad.cpu().numpy(), gref_f) <= 1e-7
+
+
+@pytest.mark.parametrize("inner", ["f32", "f32r12", "f32r12h", "f32s16"])
+def test_autograd_every_mixed_format_with_naik(q, oracle_mod, inner):
+    """StaggeredAction with the Naik term and each mixed inner format: the
+    long links go to the solver in qex_long_links_prec(inner) (16-bit with a
+    per-link step for the 16-bit formats, FP32 otherwise), and the action and
+    both gradients meet the oracle within what a 1e-10 solve allows; an
+    unknown format is rejected before anything runs."""
+    dims = (4, 4, 4, 8)
+    m = 0.15
+    s, u, w, phi = _inputs(oracle_mod, dims, True, 54, m)
+    S_ref, x = oracle_mod.action(dims, u, phi, m, w, C3)
+    y = oracle_mod.dslash_parity(dims, u, x, 1, w, C3)
+    gref_f, gref_l = oracle_mod.force(dims, u, x, y, w, C3, 1)
+    lat = q.Lattice(dims)
+    U = dev(u).requires_grad_(True)
+    W = dev(w).requires_grad_(True)
+    S = q.StaggeredAction.apply(U, W, dev(phi), lat, m, C3, inner, 1e-10)
+    S.backward()
+    assert S.item() == pytest.approx(S_ref, rel=1e-9)
+    assert relerr(U.grad.cpu().numpy(), gref_f) <= 1e-7
+    assert relerr(W.grad.cpu().numpy(), gref_l) <= 1e-7
+    with pytest.raises(ValueError):
+        q.StaggeredAction.apply(U, W, dev(phi), lat, m, C3, "bf16", 1e-10)
