@@ -262,8 +262,13 @@ qex_status qex_normal_op(const qex_lattice *lat, qex_prec prec, const void *fat,
  * - Memory: every GPU that loads the library holds the array until the
  *   process exits.
  * - Set-up: the first call made with a given device current looks up the
- *   array's device address (cudaGetSymbolAddress) for that device; make that
- *   first call before any stream capture.
+ *   array's device address (cudaGetSymbolAddress) for that device, and so
+ *   does the first call after the device's context changed (for example
+ *   after cudaDeviceReset, which can move the array); make that first call
+ *   before any stream capture.
+ * - Launch shape: the call never runs the autotuner (which allocates); it
+ *   uses the shapes the lattice already has, the compiled defaults on a
+ *   lattice no other call has tuned.
  * - Sharing: every call on every lattice uses the same array, and it keeps
  *   the last call's contents (each call overwrites what it reads).  Calls
  *   whose kernels overlap on the GPU (different streams, or host threads
@@ -440,11 +445,26 @@ qex_status qex_tune(const qex_lattice *lat, qex_prec prec, const void *fat, cons
  * persistent grid in blocks per SM (0: one thread per site), out[3] the
  * vector kernels' grid cap in blocks per SM, out[4] where they came from (0
  * compiled defaults, not tuned yet; 1 measured; 2 cache; 3 defaults kept by
- * QEX_TUNE=0), out[5] the non-reducing Dslash grid cap in resident waves (0:
+ * QEX_TUNE=0; 4 set by qex_tune_set), out[5] the non-reducing Dslash grid cap in resident waves (0:
  * one thread per site).  out is a host array of 6 ints.  Errors: QEX_ERR_ARG.
  * Paper: no counterpart.
  */
 qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int naik, int *out);
+
+/* Pin the launch shapes of (lat, prec, naik != 0), the inverse of
+ * qex_tune_info: in[0] Dslash threads per block, in[1] threads per block of
+ * the reducing variants (both 64, 128 or 256), in[2] their persistent grid in
+ * blocks per SM (0..16, 0: one thread per site), in[3] the vector kernels'
+ * grid cap in blocks per SM (1..16; 0 leaves it), in[4] the non-reducing
+ * Dslash grid cap in resident waves (0..8, 0: one thread per site).  The
+ * shapes stay until the next qex_tune of the key (the automatic tuning of the
+ * other calls does not replace them; qex_tune_info then reports source 4).
+ * Use it to reproduce FP64 reduction bits across processes (they are fixed
+ * for a given shape) or to run a chosen shape.  A cached CG graph of the
+ * lattice is dropped (the device is synchronised first).  Errors:
+ * QEX_ERR_ARG (NULL, a value out of range).
+ * Paper: no counterpart. */
+qex_status qex_tune_set(const qex_lattice *lat, qex_prec prec, int naik, const int *in);
 
 /* Number of kernels this library has launched in the calling process so far
  * (monotone counter, for accounting of the kernels in a timed region).

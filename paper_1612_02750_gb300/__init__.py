@@ -102,6 +102,7 @@ def load():
         "qex_long_links_prec": (i, [i]),
         "qex_tune": (i, [vp, i, vp, vp, vp]),
         "qex_tune_info": (i, [vp, i, i, ip]),
+        "qex_tune_set": (i, [vp, i, i, ip]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -122,7 +123,7 @@ def exported_symbols():
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
             "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_long_links_prec",
             "qex_tune",
-            "qex_tune_info", "qex_launch_count", "qex_last_error", "qex_version"]
+            "qex_tune_info", "qex_tune_set", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -471,9 +472,17 @@ def qex_tune_info(lat: Lattice, prec, naik: bool = False) -> dict:
     """Launch shapes in use for (lat, prec, naik)."""
     out = (ctypes.c_int * 6)()
     _check(load().qex_tune_info(lat.handle, _prec(prec), 1 if naik else 0, out))
-    src = {0: "default", 1: "measured", 2: "cache", 3: "disabled"}
+    src = {0: "default", 1: "measured", 2: "cache", 3: "disabled", 4: "set"}
     return {"dslash_block": out[0], "reduce_block": out[1], "reduce_blocks_per_sm": out[2],
             "blas_blocks_per_sm": out[3], "source": src.get(out[4], str(out[4])), "dslash_waves": out[5]}
+
+
+def qex_tune_set(lat: Lattice, prec, naik: bool = False, dslash_block: int = 256, reduce_block: int = 256,
+                 reduce_blocks_per_sm: int = 4, blas_blocks_per_sm: int = 0, dslash_waves: int = 0) -> None:
+    """Pin the launch shapes for (lat, prec, naik) (see qex_tune_info for the
+    fields)."""
+    arr = (ctypes.c_int * 5)(dslash_block, reduce_block, reduce_blocks_per_sm, blas_blocks_per_sm, dslash_waves)
+    _check(load().qex_tune_set(lat.handle, _prec(prec), 1 if naik else 0, arr))
 
 
 def qex_launch_count() -> int:

@@ -12,8 +12,14 @@
 // The array is part of the library's device image: every GPU that loads the
 // library holds it (kStaticScratchBytes) until the process exits.  Host code
 // must not pass the array's name to a kernel (on the host it is only a
-// stand-in symbol); the device address is looked up once per device with
-// cudaGetSymbolAddress on the first call made with that device current.
+// stand-in symbol); the device address is looked up with cudaGetSymbolAddress
+// on the first call made with a device current, and again whenever the
+// device's current CUDA context is not the one the address was taken in (a
+// cudaDeviceReset destroys the context, and the array may come back at
+// another address in the next one).  The context is identified by the
+// driver's context id, reached through the runtime's driver entry-point
+// query, so the library does not link the driver directly; without that
+// query every call looks the address up again.
 #include <mutex>
 
 #include "qex_kernels.cuh"
@@ -25,13 +31,48 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_normal_scratch[kStaticScratchBytes];
 
-static void *g_scratch_ptr[kMaxDevices];
+struct ScratchSlot {
+    void *ptr;                // device address of g_normal_scratch in that context
+    unsigned long long ctx;   // driver id of the context it was taken in (0: none)
+};
+static ScratchSlot g_scratch[kMaxDevices];
 static std::mutex g_scratch_mu;
 
 qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *fat, const void *lng,
                              const void *in, const void *out);
 
-// Device address of g_normal_scratch on the current device (set up once).
+// Id of the calling thread's current driver context, 0 if there is none or
+// the driver does not offer the two queries.  The function pointers are
+// looked up once per process.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+static unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();  // a failed query leaves no sticky error behind
+    });
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx) return 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_normal_scratch on the current device, in its current
+// context (looked up when the device has none cached for this context).
 static qex_status static_scratch(void **out) {
     int dev = 0;
     QEX_CUDA(cudaGetDevice(&dev));
@@ -40,7 +81,9 @@ static qex_status static_scratch(void **out) {
         return QEX_ERR_ARG;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    ScratchSlot &slot = g_scratch[dev];
+    if (!slot.ptr || ctx == 0 || slot.ctx != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_normal_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_normal_scratch)");
@@ -48,9 +91,12 @@ static qex_status static_scratch(void **out) {
             set_error("cudaGetSymbolAddress returned NULL for the static scratch");
             return QEX_ERR_CUDA;
         }
-        g_scratch_ptr[dev] = p;
+        slot.ptr = p;
+        // the lookup made the device's primary context current if no
+        // context was: take the id again
+        slot.ctx = ctx ? ctx : current_context_id();
     }
-    *out = g_scratch_ptr[dev];
+    *out = slot.ptr;
     return QEX_OK;
 }
 

@@ -376,3 +376,32 @@ extern "C" qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int n
     out[5] = set ? sh.ds_waves : 0;
     return QEX_OK;
 }
+
+extern "C" qex_status qex_tune_set(const qex_lattice *latc, qex_prec prec, int naik, const int *in) {
+    qex_status st;
+    if ((st = check_lattice(latc)) || (st = check_prec(prec))) return st;
+    if (!in) {
+        set_error("in must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    auto ok_block = [](int b) { return b == 64 || b == 128 || b == 256; };
+    if (!ok_block(in[0]) || !ok_block(in[1]) || in[2] < 0 || in[2] > 16 || in[3] < 0 || in[3] > 16 || in[4] < 0 ||
+        in[4] > 8) {
+        set_error("launch shape out of range: blocks 64/128/256, blocks per SM 0..16, waves 0..8");
+        return QEX_ERR_ARG;
+    }
+    qex_lattice *lat = const_cast<qex_lattice *>(latc);
+    if (lat->cg_graph) {  // its kernels carry the old launch shapes
+        cudaDeviceSynchronize();
+        free_cg_graph(lat->cg_graph);
+        lat->cg_graph = nullptr;
+    }
+    LaunchShape &sh = lat->shape[prec][naik ? 1 : 0];
+    sh.ds_block = in[0];
+    sh.red_block = in[1];
+    sh.red_per_sm = in[2];
+    sh.ds_waves = in[4];
+    if (in[3] > 0) lat->blas_per_sm = in[3];
+    lat->tuned[prec][naik ? 1 : 0] = 4;
+    return QEX_OK;
+}

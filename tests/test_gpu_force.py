@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import fieldgen as fg
+from parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -32,10 +33,6 @@ def dev(a):
     import torch
 
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-
-def relerr(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def _inputs(oracle_mod, dims, naik, seed, m, a=0.5):
@@ -65,9 +62,9 @@ def test_force_kernel_matches_oracle(q, oracle_mod, naik, kind):
     xe = q.qex_pack_field(lat, "f64", 0, dev(x))
     yo = q.qex_pack_field(lat, "f64", 1, dev(y))
     gf, gl = q.qex_force(lat, fat, lng, c3, xe, yo, kind)
-    assert relerr(q.qex_unpack_links(lat, "f64", gf).cpu().numpy(), ref_f) <= 1e-13
+    assert_close(q.qex_unpack_links(lat, "f64", gf).cpu().numpy(), ref_f, 1e-13, ("fat", naik, kind))
     if naik:
-        assert relerr(q.qex_unpack_links(lat, "f64", gl).cpu().numpy(), ref_l) <= 1e-13
+        assert_close(q.qex_unpack_links(lat, "f64", gl).cpu().numpy(), ref_l, 1e-13, ("long", kind))
 
 
 @pytest.mark.parametrize("inner,bound", [("f64", 1e-9), ("f32r12", 1e-7)])
@@ -94,9 +91,8 @@ def test_force_chain_matches_oracle(q, oracle_mod, inner, bound):
     q.qex_cg(lat, inner, fat, lng, f32, l32, C3, m, b, xg, tol=tol)
     yg = q.qex_dslash(lat, "f64", fat, lng, C3, 1, xg)
     gf, gl = q.qex_force(lat, fat, lng, C3, xg, yg, 0)
-    ef = relerr(q.qex_unpack_links(lat, "f64", gf).cpu().numpy(), ref_f)
-    el = relerr(q.qex_unpack_links(lat, "f64", gl).cpu().numpy(), ref_l)
-    assert ef <= bound and el <= bound, (ef, el)
+    assert_close(q.qex_unpack_links(lat, "f64", gf).cpu().numpy(), ref_f, bound, ("fat", inner))
+    assert_close(q.qex_unpack_links(lat, "f64", gl).cpu().numpy(), ref_l, bound, ("long", inner))
 
 
 def _action_quadratic(q, lat, fat, lng, c3, m, b, tol=1e-13):
@@ -172,8 +168,8 @@ def test_autograd_gradient(q, oracle_mod):
     S = q.StaggeredAction.apply(U, W, P, lat, m, C3, "f64", 1e-13)
     assert S.item() == pytest.approx(S_ref, rel=1e-11)
     S.backward()
-    assert relerr(U.grad.cpu().numpy(), gref_f) <= 1e-10
-    assert relerr(W.grad.cpu().numpy(), gref_l) <= 1e-10
+    assert_close(U.grad.cpu().numpy(), gref_f, 1e-10, "U.grad")
+    assert_close(W.grad.cpu().numpy(), gref_l, 1e-10, "W.grad")
     du = dev(fg.complex_gaussian(s["directions"], u.shape))
     eps = 1e-6
     with torch.no_grad():
@@ -185,7 +181,7 @@ def test_autograd_gradient(q, oracle_mod):
     S2 = q.StaggeredAction.apply(U2, W.detach(), P, lat, m, C3, "f32r12", 1e-10)
     S2.backward()
     assert S2.item() == pytest.approx(S_ref, rel=1e-9)
-    assert relerr(U2.grad.cpu().numpy(), gref_f) <= 1e-7
+    assert_close(U2.grad.cpu().numpy(), gref_f, 1e-7, "U.grad, mixed")
 
 
 @pytest.mark.parametrize("inner", ["f32", "f32r12", "f32r12h", "f32s16"])
@@ -207,7 +203,7 @@ def test_autograd_every_mixed_format_with_naik(q, oracle_mod, inner):
     S = q.StaggeredAction.apply(U, W, dev(phi), lat, m, C3, inner, 1e-10)
     S.backward()
     assert S.item() == pytest.approx(S_ref, rel=1e-9)
-    assert relerr(U.grad.cpu().numpy(), gref_f) <= 1e-7
-    assert relerr(W.grad.cpu().numpy(), gref_l) <= 1e-7
+    assert_close(U.grad.cpu().numpy(), gref_f, 1e-7, ("U.grad", inner))
+    assert_close(W.grad.cpu().numpy(), gref_l, 1e-7, ("W.grad", inner))
     with pytest.raises(ValueError):
         q.StaggeredAction.apply(U, W, dev(phi), lat, m, C3, "bf16", 1e-10)
