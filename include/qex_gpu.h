@@ -324,6 +324,25 @@ qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, con
                   void *x64, double tol, int maxiter, double delta, void *stream,
                   qex_cg_stats *stats);
 
+/* Device time of each kernel of the CG iteration, measured inside a solve
+ * (profiling): the set-up of qex_cg (same arguments and link formats), then
+ * `iters` iterations (3 <= iters <= 10000) of exactly the kernels qex_cg runs,
+ * in its order and launch shapes and on the same buffers, with an event after
+ * every kernel.  The stop test is disabled, so every kernel does its full
+ * work; no reliable update runs.  ms_out (host, room for 4) receives each
+ * kernel's average time in milliseconds over all but the first two
+ * iterations, *n_out the number of kernels per iteration: 3 for a mixed solve
+ * (direction update fused into D_oe, normal operator with <p, A p>, residual
+ * update with ||r||^2), 4 for FP64 (direction update, D_oe, normal operator,
+ * iterate and residual update).  b64 must be non-zero; x64 is the initial
+ * guess and afterwards holds an intermediate iterate (FP64) or is unchanged
+ * (mixed).  Synchronises the stream.  Errors as qex_cg, QEX_ERR_ARG for
+ * iters out of range or a zero source.
+ * Paper: no counterpart (measurement of the solver of Sec. 4 and Fig. 1). */
+qex_status qex_cg_profile(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
+                          const void *fat32, const void *lng32, double c_naik, double mass, const void *b64,
+                          void *x64, int iters, void *stream, double *ms_out, int *n_out);
+
 /* ---------------------------------------------------------------- force */
 
 /* Fermion force of the pseudofermion action S = phi^+ A^{-1} phi,

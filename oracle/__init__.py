@@ -68,6 +68,7 @@ def _load():
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         lib.oracle_force.argtypes = [i4, ctypes.c_int, vp, vp, d, vp, vp, ctypes.c_int, vp, vp]
         lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -107,6 +108,11 @@ def _ptr(a):
 def threads() -> int:
     """OpenMP threads the oracle's site loops use (OMP_NUM_THREADS)."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's later site loops (timing only)."""
+    _load().oracle_set_threads(int(n))
 
 
 def eo_table(dims) -> np.ndarray:

@@ -416,3 +416,13 @@ int oracle_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the later site loops (timing only; the results do not depend on
+ * it, each site's sum being formed by one thread). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -95,6 +95,7 @@ def load():
         "qex_dot": (i, [vp, i, vp, vp, vp, vp]),
         "qex_cg": (i, [vp, i, vp, vp, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_cg_host": (i, [vp, i, vp, vp, d, d, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_cg_profile": (i, [vp, i, vp, vp, vp, vp, d, d, vp, vp, i, vp, ctypes.POINTER(d), ip]),
         "qex_force": (i, [vp, vp, vp, d, vp, vp, i, vp, vp, vp]),
         "qex_dslash_mrhs": (i, [vp, i, vp, vp, d, i, i, vp, vp, vp]),
         "qex_cg_mrhs": (i, [vp, i, vp, vp, vp, vp, d, d, i, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
@@ -121,7 +122,7 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_long_links_prec",
+            "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_long_links_prec",
             "qex_tune",
             "qex_tune_info", "qex_tune_set", "qex_launch_count", "qex_last_error", "qex_version"]
 
@@ -368,6 +369,18 @@ def qex_cg(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, mass:
     if check:
         _check(st)
     return st, stats.as_dict()
+
+
+def qex_cg_profile(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: float, mass: float, b64, x64,
+                   iters: int = 50, stream=None):
+    """Average device time (ms) of each kernel of the CG iteration inside a
+    solve: a list of 3 (mixed) or 4 (FP64) numbers in launch order."""
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int(0)
+    _check(load().qex_cg_profile(lat.handle, _prec(inner), _ptr(fat64), _ptr(lng64), _ptr(fat32), _ptr(lng32),
+                                 float(c_naik), float(mass), _ptr(b64), _ptr(x64), int(iters), _stream(stream), ms,
+                                 ctypes.byref(n)))
+    return [ms[k] for k in range(n.value)]
 
 
 # -------------------------------------------------------------------- force

@@ -102,8 +102,20 @@ struct Solve {
 // links the D_oe launch before it read last (still in L2).
 static const bool reverse_second = QEX_REVERSE_SECOND != 0;
 
+// Events recorded after each kernel of an iteration (profiling only).
+struct Marks {
+    cudaEvent_t *ev;  // one per kernel of the iteration, NULL: none
+    int n;
+};
+
+static qex_status mark(const Marks *m, int k, cudaStream_t st) {
+    if (m && m->ev && k < m->n) QEX_CUDA(cudaEventRecord(m->ev[k], st));
+    return QEX_OK;
+}
+
 // One CG iteration in the inner precision, every kernel halt-checked.
-static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t st) {
+// marks: an event recorded after each kernel (k = 0, 1, ...), or NULL.
+static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t st, const Marks *marks = nullptr) {
     qex_lattice *lat = s.lat;
     CgScalars *S = lat->scalars;
     DslashArgs a = {};
@@ -120,6 +132,7 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
     void *pb[2] = {s.mixed ? (void *)s.B.p32[0] : (void *)s.B.p64[0],
                    s.mixed ? (void *)s.B.p32[1] : (void *)s.B.p64[1]};
     qex_status err;
+    int k = 0;
     a.out_parity = 1;
     a.out = tmp;
     a.r = r;
@@ -137,10 +150,12 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
         // FP64: the Dslash is FP64-ALU bound, so the update is its own
         // memory-bound pass instead of eight recomputations per site
         if ((err = launch_update_p(lat, a.prec, r, pb, S, st))) return err;
+        if ((err = mark(marks, k++, st))) return err;
         a.epi = EPI_PLAIN;
         a.psel = 1;
     }
     if ((err = launch_dslash(lat, a, st))) return err;
+    if ((err = mark(marks, k++, st))) return err;
     a.out_parity = 0;
     a.in = tmp;
     a.out = ap;
@@ -149,7 +164,9 @@ static qex_status enqueue_iteration(Solve &s, const GraphCtl &ctl, cudaStream_t 
     a.m2 = s.m2;
     a.reverse = reverse_second ? 1 : 0;
     if ((err = launch_dslash(lat, a, st))) return err;
-    return launch_update_xr(lat, a.prec, x, r, pb, ap, S, ctl, st);
+    if ((err = mark(marks, k++, st))) return err;
+    if ((err = launch_update_xr(lat, a.prec, x, r, pb, ap, S, ctl, st))) return err;
+    return mark(marks, k, st);
 }
 
 // FP64 true residual r64 = b - A x64 (after folding x_hat into x64), then the
@@ -505,4 +522,99 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
         stats->time_ms = ms;
     }
     return result;
+}
+
+// Device time of each kernel of the CG iteration, measured inside a solve:
+// the same set-up as qex_cg (initial FP64 residual), then `iters` iterations
+// of exactly the kernels the solve runs, in its order and with its launch
+// shapes, enqueued back to back with an event after every kernel.  The stop
+// test is disabled (tol 0, no reliable update before `iters`), so every
+// timed kernel does its full work.
+extern "C" qex_status qex_cg_profile(const qex_lattice *latc, qex_prec inner, const void *fat64, const void *lng64,
+                                     const void *fat32, const void *lng32, double c_naik, double mass,
+                                     const void *b64, void *x64, int iters, void *stream, double *ms_out,
+                                     int *n_out) {
+    qex_status st;
+    if ((st = check_lattice(latc)) || (st = check_prec(inner))) return st;
+    const bool mixed = inner != QEX_F64;
+    if ((st = check_dslash_args(latc, QEX_F64, fat64, lng64, b64, x64))) return st;
+    if (mixed && (!fat32 || !aligned16(fat32) || (lng64 && (!lng32 || !aligned16(lng32))))) {
+        set_error("mixed precision needs aligned FP32 copies of the fat (and long) links");
+        return QEX_ERR_ARG;
+    }
+    if (iters < 3 || iters > 10000 || !ms_out || !n_out) {
+        set_error("need 3 <= iters <= 10000 and non-NULL ms_out, n_out");
+        return QEX_ERR_ARG;
+    }
+    qex_lattice *lat = const_cast<qex_lattice *>(latc);
+    if ((st = ensure_scratch(lat))) return st;
+    Solve s;
+    s.lat = lat;
+    s.mixed = mixed;
+    s.inner = inner;
+    s.fat64 = fat64;
+    s.lng64 = lng64;
+    s.fat32 = mixed ? fat32 : nullptr;
+    s.lng32 = mixed ? lng32 : nullptr;
+    s.c3 = c_naik;
+    s.m2 = mass * mass;
+    s.b64 = (const double *)b64;
+    s.x64 = (double *)x64;
+    s.defer_x = mixed && QEX_DEFER_X != 0;
+    const cudaStream_t cst = as_stream(stream);
+    if ((st = ensure_tuned(lat, inner, mixed ? fat32 : fat64, mixed ? lng32 : lng64, cst, false))) return st;
+    if (mixed && (st = ensure_tuned(lat, QEX_F64, fat64, lng64, cst, false))) return st;
+    if ((st = carve(lat, mixed, s.B))) return st;
+    lat->pdl = 0;  // an event between kernels would cut programmatic overlap anyway
+    CgScalars init;
+    memset(&init, 0, sizeof(init));
+    init.tol2 = 0.0;    // never met: every iteration runs
+    init.delta2 = 0.0;  // no reliable update
+    init.maxiter = iters;
+    QEX_CUDA(cudaStreamSynchronize(cst));
+    *lat->scalars_host = init;
+    QEX_CUDA(cudaMemcpyAsync(lat->scalars, lat->scalars_host, sizeof(CgScalars), cudaMemcpyHostToDevice, cst));
+    const size_t fbytes = (size_t)lat->vh * (mixed ? 24 : 48);
+    for (int k = 0; k < 2; ++k)
+        QEX_CUDA(cudaMemsetAsync(mixed ? (void *)s.B.p32[k] : (void *)s.B.p64[k], 0, fbytes, cst));
+    if (mixed) QEX_CUDA(cudaMemsetAsync(s.B.xh32, 0, fbytes, cst));
+    const GraphCtl off = {};
+    if ((st = launch_norm2(lat, QEX_F64, b64, nullptr, lat->scalars, cst))) return st;
+    if ((st = launch_any_nonzero(lat, (const double *)x64, &lat->scalars->x_nonzero, cst))) return st;
+    if ((st = enqueue_reliable_update(s, off, cst, true))) return st;
+    if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
+    if (!(lat->scalars_host->bb > 0.0) || !isfinite(lat->scalars_host->bb)) {
+        set_error("qex_cg_profile needs a non-zero, finite source");
+        return QEX_ERR_ARG;
+    }
+    const int nk = mixed ? 3 : 4;
+    const int nev = iters * nk + 1;
+    cudaEvent_t *ev = new cudaEvent_t[nev];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < nev && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e != cudaSuccess) --made;
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], cst);
+    for (int it = 0; it < iters && e == cudaSuccess && !st; ++it) {
+        Marks m = {ev + 1 + it * nk, nk};
+        st = enqueue_iteration(s, off, cst, &m);
+    }
+    if (e == cudaSuccess && !st) e = cudaEventSynchronize(ev[nev - 1]);
+    if (e == cudaSuccess && !st) {
+        // average over all but the first two iterations
+        for (int j = 0; j < nk; ++j) ms_out[j] = 0.0;
+        for (int it = 2; it < iters; ++it)
+            for (int j = 0; j < nk; ++j) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[it * nk + j], ev[it * nk + j + 1]);
+                ms_out[j] += ms;
+            }
+        for (int j = 0; j < nk; ++j) ms_out[j] /= (iters - 2);
+        *n_out = nk;
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    delete[] ev;
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "qex_cg_profile events");
+    return QEX_OK;
 }
