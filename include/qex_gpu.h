@@ -72,7 +72,7 @@ typedef enum {
     QEX_ERR_ALIGN = 3,           /* pointer not 16-byte aligned */
     QEX_ERR_CUDA = 4,            /* a CUDA runtime call failed (message in qex_last_error) */
     QEX_ERR_NOT_CONVERGED = 5,   /* solver hit maxiter; the result so far is returned */
-    QEX_ERR_TIMEOUT = 6,         /* reserved for bounded device-side waits */
+    QEX_ERR_TIMEOUT = 6,         /* a bounded device-side wait ran out */
     QEX_ERR_NAN = 7              /* NaN/Inf met in a reduction, or CG breakdown */
 } qex_status;
 
@@ -313,8 +313,10 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  * Returns QEX_ERR_NOT_CONVERGED after maxiter iterations (x64 holds the last
  * iterate), QEX_ERR_NAN on a NaN/Inf or a non-positive <p, A p>,
  * QEX_ERR_TIMEOUT if a grid barrier of the persistent kernel waited longer
- * than about a second (blocks not co-resident; the kernel returns instead of
- * waiting forever).
+ * than its limit (blocks not co-resident; the kernel returns instead of
+ * waiting forever; the message says how many of its blocks left it).  The
+ * limit is about a second (2e9 clock64 cycles); the environment variable
+ * QEX_BARRIER_TIMEOUT_CYCLES sets another (read at each launch).
  * Paper: Sec. 4 (single and double precision conjugate-gradient solvers of the
  * staggered Dirac matrix) and Fig. 1 (one right-hand side); the mixed solve
  * with FP64 reliable updates is this library's combination of the two.

@@ -454,10 +454,11 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
             if ((st = launch_cg_fused(lat, inner, s.fat32, s.lng32, s.c3, s.m2, s.B.xh32, s.B.r32, s.B.p32, s.B.ap32,
                                       s.B.tmp32, cst)))
                 return st;
-            int timed_out = 0;
-            if ((st = fused_barrier_status(lat, cst, &timed_out))) return st;
+            int timed_out = 0, exited = 0;
+            if ((st = fused_barrier_status(lat, cst, &timed_out, &exited))) return st;
             if (timed_out) {
-                set_error("fused CG: a grid barrier timed out");
+                set_error("fused CG: a grid barrier timed out (%d of %d blocks left the kernel)", exited,
+                          lat->fused_blocks);
                 result = QEX_ERR_TIMEOUT;
                 break;
             }

@@ -21,10 +21,14 @@
 // Grid barriers: arrival counters (per group of 32 blocks, then across the
 // groups) and a generation word, reset by the host before each launch; the
 // last block to arrive bumps the generation.  A wait
-// that lasts longer than about a second (clock64) records a timeout in the
-// error word and every block leaves at its next barrier, so a barrier can
-// never hang the GPU; the host then reports QEX_ERR_TIMEOUT.
+// that lasts longer than a limit (clock64 cycles, about a second by default;
+// the environment variable QEX_BARRIER_TIMEOUT_CYCLES sets another, which the
+// tests use to make the limit run out) records a timeout in the error word
+// and every block leaves at its next barrier, so a barrier can never hang the
+// GPU; each block counts itself out on leaving, and the host then reports
+// QEX_ERR_TIMEOUT with the count.
 #include <math.h>
+#include <stdlib.h>
 
 #include "qex_dslash_site.cuh"
 #include "qex_kernels.cuh"
@@ -42,6 +46,8 @@ struct FusedArgs {
     unsigned int *bar_count;     // barrier counters: top at [0], group g at [(g + 1) * 32]
     unsigned int *bar_gen;       // barriers completed in this launch
     int *bar_err;                // nonzero: a barrier timed out
+    unsigned int *exited;        // blocks that have left the kernel
+    long long timeout_cycles;    // longest wait at a barrier
 };
 
 constexpr int kFusedBlock = 256;  // most threads per block (launch bounds)
@@ -51,7 +57,7 @@ constexpr int kFusedBlock = 256;  // most threads per block (launch bounds)
 #ifndef QEX_FUSED_SPIN_NS
 #define QEX_FUSED_SPIN_NS 0  // sleep between polls of a barrier (0: poll back to back)
 #endif
-constexpr long long kBarrierTimeoutCycles = 2000000000ll;  // about one second at 2 GHz
+constexpr long long kBarrierTimeoutCycles = 2000000000ll;  // default limit: about one second at 2 GHz
 
 // Grid barrier number `gen + 1`; false if some block timed out (then every
 // block leaves at its next barrier).  Two levels: a block arrives at the
@@ -63,7 +69,7 @@ constexpr int kBarrierGroup = 32;
 constexpr int kBarrierStride = 32;  // unsigned words between counters (128 bytes)
 
 __device__ __forceinline__ bool fused_barrier(unsigned int *counters, unsigned int *gen_word, int *err,
-                                              unsigned int gen) {
+                                              unsigned int gen, long long timeout_cycles) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -87,7 +93,7 @@ __device__ __forceinline__ bool fused_barrier(unsigned int *counters, unsigned i
             const long long t0 = clock64();
             while (*gv != gen + 1) {
                 if (*ev != 0) break;
-                if (clock64() - t0 > kBarrierTimeoutCycles) {
+                if (clock64() - t0 > timeout_cycles) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -150,7 +156,7 @@ struct FusedState {
 };
 
 template <typename R, int FMT, bool NAIK>
-__global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_kernel(const FusedArgs<R> A) {
+__device__ __forceinline__ void cg_fused_body(const FusedArgs<R> &A) {
     __shared__ double smem[32];
     __shared__ FusedState st;
     CgScalars *S = A.S;
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_ke
                 store_vec(pnew, vh, i, axpy_vec_cg(A.r, pold, b, vh, i));
             }
         }
-        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
+        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++, A.timeout_cycles)) return;
         {   // 2. A p_new = m^2 p_new - D_eo tmp; <p_new, A p_new>
             double part = 0.0;
             for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += stride) {
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_ke
             const double bs = block_sum(part, smem);
             if (threadIdx.x == 0) A.partials[blockIdx.x] = bs;
         }
-        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
+        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++, A.timeout_cycles)) return;
         {
             const double pAp = fused_total(A.partials, nb, smem);
             if (threadIdx.x == 0) {
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_ke
             const double bs = block_sum(part, smem);
             if (threadIdx.x == 0) A.partials[nb + blockIdx.x] = bs;
         }
-        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++)) return;
+        if (!fused_barrier(A.bar_count, A.bar_gen, A.bar_err, gen++, A.timeout_cycles)) return;
         {
             const double rr_new = fused_total(A.partials + nb, nb, smem);
             if (threadIdx.x == 0) {
@@ -282,6 +288,13 @@ __global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_ke
 }
 
 template <typename R, int FMT, bool NAIK>
+__global__ void __launch_bounds__(kFusedBlock, QEX_FUSED_MIN_BLOCKS) cg_fused_kernel(const FusedArgs<R> A) {
+    cg_fused_body<R, FMT, NAIK>(A);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(A.exited, 1u);  // every way out of the body ends here
+}
+
+template <typename R, int FMT, bool NAIK>
 static qex_status launch_fused_t(qex_lattice *lat, const FusedArgs<R> &A0, cudaStream_t st) {
     auto kernel = cg_fused_kernel<R, FMT, NAIK>;
     int per_sm = 0;
@@ -307,12 +320,19 @@ static qex_status launch_fused_t(qex_lattice *lat, const FusedArgs<R> &A0, cudaS
     }
     unsigned int *bar = reinterpret_cast<unsigned int *>(lat->partials + 2 * (size_t)nb + 16);
     QEX_CUDA(cudaMemsetAsync(bar, 0, bar_words * sizeof(unsigned int), st));
-    QEX_CUDA(cudaMemsetAsync(lat->counter + 3, 0, sizeof(unsigned int), st));
+    QEX_CUDA(cudaMemsetAsync(lat->counter + 3, 0, 2 * sizeof(unsigned int), st));  // error word, exit count
     FusedArgs<R> A = A0;
     A.partials = lat->partials;
     A.bar_count = bar;
     A.bar_gen = bar + (size_t)(ngroups + 1) * kBarrierStride;
     A.bar_err = reinterpret_cast<int *>(lat->counter + 3);
+    A.exited = lat->counter + 4;
+    A.timeout_cycles = kBarrierTimeoutCycles;
+    if (const char *e = getenv("QEX_BARRIER_TIMEOUT_CYCLES")) {
+        const long long v = atoll(e);
+        if (v > 0) A.timeout_cycles = v;
+    }
+    lat->fused_blocks = nb;
     void *args[] = {&A};
     QEX_CUDA(cudaLaunchCooperativeKernel((const void *)kernel, dim3(nb), dim3(block), args, 0, st));
     note_launch();
@@ -350,12 +370,14 @@ qex_status launch_cg_fused(qex_lattice *lat, qex_prec inner, const void *fat32, 
     }
 }
 
-// Whether a barrier of the last fused run timed out (reads the error word).
-qex_status fused_barrier_status(qex_lattice *lat, cudaStream_t st, int *timed_out) {
-    int v = 0;
-    QEX_CUDA(cudaMemcpyAsync(&v, lat->counter + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+// Whether a barrier of the last fused run timed out (reads the error word),
+// and how many of its blocks left the kernel.
+qex_status fused_barrier_status(qex_lattice *lat, cudaStream_t st, int *timed_out, int *exited) {
+    unsigned int v[2] = {0u, 0u};
+    QEX_CUDA(cudaMemcpyAsync(v, lat->counter + 3, sizeof(v), cudaMemcpyDeviceToHost, st));
     QEX_CUDA(cudaStreamSynchronize(st));
-    *timed_out = v != 0;
+    *timed_out = v[0] != 0;
+    if (exited) *exited = (int)v[1];
     return QEX_OK;
 }
 

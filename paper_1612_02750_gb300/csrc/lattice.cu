@@ -93,8 +93,8 @@ qex_status ensure_scratch(qex_lattice *lat) {
     const int mrhs = (sm_count() * 8 + 1) * kMaxRhs;  // per-block, per-right-hand-side partials
     if (lat->partials_len < mrhs) lat->partials_len = mrhs;
     QEX_CUDA(cudaMalloc(&lat->partials, sizeof(double) * lat->partials_len));
-    QEX_CUDA(cudaMalloc(&lat->counter, sizeof(unsigned int) * 4));
-    QEX_CUDA(cudaMemset(lat->counter, 0, sizeof(unsigned int) * 4));
+    QEX_CUDA(cudaMalloc(&lat->counter, sizeof(unsigned int) * 8));
+    QEX_CUDA(cudaMemset(lat->counter, 0, sizeof(unsigned int) * 8));
     QEX_CUDA(cudaMalloc(&lat->red_out, sizeof(double) * 8));
     QEX_CUDA(cudaMalloc(&lat->scalars, sizeof(CgScalars)));
     QEX_CUDA(cudaMallocHost(&lat->scalars_host, sizeof(CgScalars)));

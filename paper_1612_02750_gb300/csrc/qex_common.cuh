@@ -533,6 +533,7 @@ struct qex_lattice {
     int tuned[5][2];           // 0 no, 1 measured, 2 from the cache, 3 defaults (QEX_TUNE=0)
     int blas_per_sm;           // 0: QEX_BLAS_BLOCKS_PER_SM
     int pdl;                   // CG kernels launch with programmatic dependent launch (set by qex_cg)
+    int fused_blocks;          // grid of the last fused CG launch
 };
 
 namespace qex {

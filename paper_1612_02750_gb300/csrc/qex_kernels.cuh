@@ -144,8 +144,9 @@ qex_status launch_dot(qex_lattice *lat, qex_prec prec, const void *a, const void
 // is due or an error, then writes the CG scalars back (halt set).
 qex_status launch_cg_fused(qex_lattice *lat, qex_prec inner, const void *fat32, const void *lng32, double c3, double m2,
                            float *x, float *r, float *const p[2], float *ap, float *tmp, cudaStream_t st);
-// Synchronises st and reports whether a grid barrier of the last fused run timed out.
-qex_status fused_barrier_status(qex_lattice *lat, cudaStream_t st, int *timed_out);
+// Synchronises st and reports whether a grid barrier of the last fused run
+// timed out, and how many of its blocks left the kernel (exited may be NULL).
+qex_status fused_barrier_status(qex_lattice *lat, cudaStream_t st, int *timed_out, int *exited);
 
 int blas_blocks(const qex_lattice *lat);
 int sm_count();

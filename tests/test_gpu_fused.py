@@ -95,3 +95,30 @@ def test_fused_solve_edges(q, monkeypatch):
     runs = [_solve(q, lat, "f32r12h", fat64, None, fati, None, 0.0, 0.05, bh, tol=1e-10, delta=0.1)[2]
             for _ in range(2)]
     assert torch.equal(runs[0], runs[1])
+
+
+def test_fused_barrier_limit_runs_out_and_the_lattice_recovers(q, oracle_mod, monkeypatch):
+    """The persistent kernel's grid barriers give up after a limit of clock64
+    cycles.  With the limit set to 100 cycles (a barrier of 32 blocks takes
+    longer) some wait runs out: qex_cg returns QEX_ERR_TIMEOUT (6), every
+    block has left the kernel, and the next solve on the same lattice, with
+    the default limit of about a second, converges to the oracle's true
+    residual."""
+    import re
+
+    dims = (8, 8, 8, 16)  # Vh = 4096: 32 blocks of 128 threads
+    m = 0.1
+    lat, u, w, b, fat64, lng64, fati, lngi = _setup(q, dims, False, "f32r12h", 81)
+    bh = q.qex_pack_field(lat, "f64", 0, dev(b))
+    monkeypatch.setenv("QEX_CG_MODE", "fused")
+    monkeypatch.setenv("QEX_BARRIER_TIMEOUT_CYCLES", "100")
+    st, stats, x = _solve(q, lat, "f32r12h", fat64, lng64, fati, lngi, 0.0, m, bh, tol=1e-10, delta=0.1)
+    msg = q.qex_last_error()
+    assert st == 6 and not stats["converged"], (st, stats, msg)
+    left = re.search(r"\((\d+) of (\d+) blocks left", msg)
+    assert left and left.group(1) == left.group(2) and int(left.group(2)) > 1, msg
+    monkeypatch.delenv("QEX_BARRIER_TIMEOUT_CYCLES")
+    st, stats, x = _solve(q, lat, "f32r12h", fat64, lng64, fati, lngi, 0.0, m, bh, tol=1e-10, delta=0.1)
+    assert st == 0 and stats["converged"], stats
+    xf = q.qex_unpack_field(lat, "f64", 0, x).cpu().numpy()
+    assert oracle_mod.true_residual(dims, u, b, xf, m) <= 1.05e-10
