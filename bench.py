@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="multi-lattice case: 8 lattices 8^4 .. 32^4, Haar links, masses 0.005 * 20^(k/7), one "
                          "batched solve against sequential single-lattice solves")
+    ap.add_argument("--profile-iteration", action="store_true",
+                    help="profiling case: one mixed-precision solve of the workload, driven from the host (the "
+                         "graph solve's kernels launched one by one), inside cudaProfilerStart/Stop")
     ap.add_argument("--dslash-only", action="store_true",
                     help="profiling case: two launches each of the 16-bit two-row, two-row FP32, FP32 and FP64 "
                          "one-hop Dslash on the workload, no timing")
@@ -196,16 +199,27 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def files_hash(rels) -> str:
+    """Hash of whole source files (kernels outside dslash.cu)."""
+    h = hashlib.sha256()
+    for rel in rels:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the capture."""
+    kernel source changed since the capture (the Dslash device code, or the
+    files a record names in "hash_files")."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)[kernel_key]
     except (OSError, KeyError, ValueError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    want = files_hash(rec["hash_files"]) if "hash_files" in rec else kernel_source_hash()
+    if rec.get("source_hash") != want:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -500,6 +514,36 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile_iteration():
+    """One warm solve (tuning, graph), then one host-driven solve of the same
+    kernels between cudaProfilerStart and cudaProfilerStop, for
+    ``ncu --profile-from-start off``."""
+    import torch
+
+    import fieldgen as fg
+    import paper_1612_02750_gb300 as q
+    from paper_1612_02750_gb300 import build as qbuild
+
+    qbuild.build()
+    wl = fg.workload(WORKLOAD)
+    u, b = make_inputs(wl)
+    lat = q.Lattice(wl["dims"], antiperiodic=True)
+    fat64 = q.qex_pack_links(lat, "f64", torch.from_numpy(u).cuda())
+    fat16 = q.qex_convert_links(lat, "f64", fat64, INNER)
+    bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
+    x = torch.zeros_like(bh)
+    q.qex_cg(lat, INNER, fat64, None, fat16, None, 0.0, wl["mass"], bh, x, tol=TOL, maxiter=200000, delta=DELTA)
+    os.environ["QEX_CG_MODE"] = "host"
+    x.zero_()
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    _, st = q.qex_cg(lat, INNER, fat64, None, fat16, None, 0.0, wl["mass"], bh, x, tol=TOL, maxiter=200000,
+                     delta=DELTA)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print("profile-iteration done", json.dumps(st))
+
+
 def run_dslash_only():
     import torch
 
@@ -761,6 +805,8 @@ def main():
         run_sweep(args)
     elif args.dslash_only:
         run_dslash_only()
+    elif args.profile_iteration:
+        run_profile_iteration()
     elif args.impl == "reference":
         run_reference(args)
     else:

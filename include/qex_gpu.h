@@ -404,8 +404,8 @@ typedef struct {
 
 /* Batched CG over n independent lattices (different extents, links and
  * masses): every kernel of an iteration is one launch over a work list of
- * (lattice, 256-site tile) items of all running lattices, so small lattices
- * share the GPU.  Each lattice has its own alpha, beta, residual norms,
+ * (lattice, tile) items of all running lattices, so small lattices share
+ * the GPU (tile size and grid: qex_cg_batch_tune_info).  Each lattice has its own alpha, beta, residual norms,
  * reliable updates and FP64 true-residual stop (tol, maxiter and delta are
  * common); the lattices iterate in lockstep and a converged one stops.  The
  * scratch of the batch (descriptors, scalars, per-tile partials) is owned by
@@ -418,6 +418,27 @@ typedef struct {
  */
 qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inner, double tol, int maxiter, double delta,
                         void *stream, qex_cg_stats *stats);
+
+/* Launch shape of the batched solver for batches led by lead (items[0].lat).
+ * The iteration kernels run a persistent grid of out[0] resident blocks of
+ * 256 threads per SM (1..3) over work items of out[1] groups of 256
+ * consecutive sites of one lattice (1, 2 or 4).  Unless pinned
+ * (qex_cg_batch_tune_set) or QEX_TUNE=0, the first qex_cg_batch call for a
+ * (set of extents and boundaries in item order, inner precision, Naik) key
+ * times the two Dslash kernels of an iteration for all nine (blocks per SM,
+ * groups per item) pairs after the first FP64 residual and keeps the fastest
+ * for the rest of the process.  Reductions are formed per 256-site group in a
+ * fixed order, so every shape gives bit-identical results.  out[2]: where the
+ * last batch's shape came from (0 none yet, 1 measured, 2 the process cache,
+ * 3 defaults under QEX_TUNE=0, 4 pinned).  out is a host array of 3 ints.
+ * Errors: QEX_ERR_ARG.
+ * Paper: no counterpart (a GPU launch-configuration search). */
+qex_status qex_cg_batch_tune_info(const qex_lattice *lead, int *out);
+
+/* Pin the batch launch shape for batches led by lead: blocks_per_sm 1..3,
+ * groups_per_item 1, 2 or 4; (0, 0) removes the pin.  Errors: QEX_ERR_ARG.
+ * Paper: no counterpart. */
+qex_status qex_cg_batch_tune_set(const qex_lattice *lead, int blocks_per_sm, int groups_per_item);
 
 /* End-to-end solve from HOST memory (the call for users whose fields live
  * on the host).  host_fat (and host_lng, or NULL) are canonical complex-double

@@ -100,6 +100,8 @@ def load():
         "qex_dslash_mrhs": (i, [vp, i, vp, vp, d, i, i, vp, vp, vp]),
         "qex_cg_mrhs": (i, [vp, i, vp, vp, vp, vp, d, d, i, vp, vp, d, i, d, vp, ctypes.POINTER(CgStats)]),
         "qex_cg_batch": (i, [i, ctypes.POINTER(CgItem), i, d, i, d, vp, ctypes.POINTER(CgStats)]),
+        "qex_cg_batch_tune_info": (i, [vp, ip]),
+        "qex_cg_batch_tune_set": (i, [vp, i, i]),
         "qex_long_links_prec": (i, [i]),
         "qex_tune": (i, [vp, i, vp, vp, vp]),
         "qex_tune_info": (i, [vp, i, i, ip]),
@@ -122,9 +124,9 @@ def exported_symbols():
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
             "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
-            "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch", "qex_long_links_prec",
-            "qex_tune",
-            "qex_tune_info", "qex_tune_set", "qex_launch_count", "qex_last_error", "qex_version"]
+            "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch",
+            "qex_cg_batch_tune_info", "qex_cg_batch_tune_set", "qex_long_links_prec", "qex_tune", "qex_tune_info",
+            "qex_tune_set", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -537,6 +539,19 @@ def qex_cg_batch(items, inner, tol: float = 1e-10, maxiter: int = 100000, delta:
     if check:
         _check(st)
     return st, [stats[k].as_dict() for k in range(n)]
+
+
+def qex_cg_batch_tune_info(lead: Lattice) -> dict:
+    """Launch shape of the last batch led by ``lead`` (see the C header)."""
+    out = (ctypes.c_int * 3)()
+    _check(load().qex_cg_batch_tune_info(lead.handle, out))
+    src = {0: "none", 1: "measured", 2: "cache", 3: "disabled", 4: "set"}
+    return {"blocks_per_sm": out[0], "groups_per_item": out[1], "source": src.get(out[2], str(out[2]))}
+
+
+def qex_cg_batch_tune_set(lead: Lattice, blocks_per_sm: int, groups_per_item: int) -> None:
+    """Pin the batch launch shape for batches led by ``lead`` ((0, 0) unpins)."""
+    _check(load().qex_cg_batch_tune_set(lead.handle, int(blocks_per_sm), int(groups_per_item)))
 
 
 def qex_last_error() -> str:

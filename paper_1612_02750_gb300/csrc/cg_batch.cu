@@ -1,6 +1,6 @@
 // cg_batch.cu -- conjugate gradient on many independent lattices at once
 // (different extents, masses and links), every launch covering a work list of
-// (lattice, 256-site tile) items.
+// (lattice, tile) items.
 //
 // Small lattices cannot fill the GPU on their own; batching them makes every
 // kernel of an iteration one launch over the tiles of all running lattices.
@@ -9,8 +9,13 @@
 // direction buffers).  The iteration kernels run a persistent grid over a
 // device-resident list of the running lattices' tiles, which the reliable
 // update recompacts whenever a lattice meets its FP64 true residual, so a
-// finished lattice costs nothing afterwards.  Reductions are per tile, summed
-// per lattice in tile order by the last block (bit-reproducible).  By
+// finished lattice costs nothing afterwards.  A tile is `spt` groups of 256
+// consecutive even-odd sites of one lattice (256 threads, one site per thread
+// and group), and the persistent grid has `per_sm` resident blocks per SM;
+// both are chosen per set of extents by timing the iteration's Dslash
+// kernels at the start of the solve (or pinned, qex_cg_batch_tune_set).
+// Reductions are per 256-site group, summed per lattice in group order by the
+// last block, so the result is bit-identical for every shape.  By
 // default the loop is one CUDA graph: a conditional WHILE node around the
 // three iteration kernels and a conditional IF node holding the reliable
 // update of the lattices that asked for one; QEX_CG_MODE=host drives the same
@@ -19,6 +24,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "qex_dslash_site.cuh"
@@ -26,12 +34,13 @@
 
 namespace qex {
 
-constexpr int kTile = 256;  // sites per tile
+constexpr int kTile = 256;  // sites per group (threads per block)
 constexpr int kBatchMinBlocks = 3;  // resident blocks per SM of the iteration kernels (no spills at 85 registers)
+constexpr int kMaxSpt = 4;          // groups per work item
 
 struct LatDesc {
     Geom g;
-    int tile0, ntiles;  // in the full tile list
+    int tile0, ntiles;  // 256-site groups: first in the full group list, count
     const void *fat_in, *lng_in;  // inner-precision links
     const double *fat64, *lng64;
     const double *b;
@@ -45,7 +54,9 @@ struct BatchScalars {
         rmax2[kMaxRhs], true_rr[kMaxRhs];
     int active[kMaxRhs], done[kMaxRhs], need[kMaxRhs], iters[kMaxRhs];
     int alist[kMaxRhs];       // running lattices, in lattice order
-    int astart[kMaxRhs + 1];  // their first tile in the compacted list; astart[nlist] = tiles
+    int astart[kMaxRhs + 1];  // their first group in the compacted group list; astart[nlist] = groups
+    int bstart[kMaxRhs + 1];  // their first work item (spt groups) in the compacted list
+    int spt;                  // groups per work item
     int nlist;
     double tol2, delta2;
     int n, iter, maxiter, halt, error, any_need, nactive, reliable_updates, trips;
@@ -85,16 +96,19 @@ __device__ __forceinline__ int lattice_of_full_tile(const LatDesc *d, int n, int
 
 // Rebuild the running-lattice list from the active flags (one thread).
 __device__ __forceinline__ void compact_list(BatchScalars *S, const LatDesc *d, int n) {
-    int k = 0, t = 0;
+    int k = 0, t = 0, w = 0;
     for (int l = 0; l < n; ++l)
         if (S->active[l]) {
             S->alist[k] = l;
             S->astart[k] = t;
+            S->bstart[k] = w;
             t += d[l].ntiles;
+            w += (d[l].ntiles + S->spt - 1) / S->spt;
             ++k;
         }
     S->nlist = k;
     S->astart[k] = t;
+    S->bstart[k] = w;
 }
 
 __device__ __forceinline__ void set_conds(const GraphCtl &ctl, unsigned int loop, unsigned int ru) {
@@ -140,19 +154,24 @@ batch_iter_dslash_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, dou
     __shared__ double tot[kMaxRhs];
     if (S->halt) return;  // uniform over the grid
     const int nl = S->nlist;
-    const int ntiles = S->astart[nl];
+    const int nitems = S->bstart[nl];
+    const int spt = S->spt;
     const int it = S->iter;
-    // blocks beyond the running tiles leave at once (the last running lattice
-    // can be a few tiles against a grid sized for all of them)
-    const unsigned int nblk = ntiles < (int)gridDim.x ? (unsigned int)ntiles : gridDim.x;
+    // blocks beyond the running work items leave at once (the last running
+    // lattice can be a few items against a grid sized for all of them)
+    const unsigned int nblk = nitems < (int)gridDim.x ? (unsigned int)nitems : gridDim.x;
     if (blockIdx.x >= nblk) return;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int k = find_start(S->astart, nl, t);
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x)
+    for (int q = 0; q < spt; ++q) {
+        const int k = find_start(S->bstart, nl, w);
         const int l = S->alist[k];
         const LatDesc &D = descs[l];
+        const int grp = (w - S->bstart[k]) * spt + q;  // group within the lattice
+        if (grp >= D.ntiles) break;                     // uniform over the block
+        const int t = S->astart[k] + grp;               // group in the compacted list
         const Geom &g = D.g;
         const size_t vh = (size_t)g.vh;
-        const int i = (t - S->astart[k]) * kTile + threadIdx.x;
+        const int i = grp * kTile + threadIdx.x;
         const R *pold = (const R *)((it & 1) ? D.p1 : D.p0);
         R *pnew = (R *)((it & 1) ? D.p0 : D.p1);
         double part = 0.0;
@@ -222,15 +241,20 @@ batch_update_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *
     // fail-safe: stop unless the last block sets the conditions again
     if (blockIdx.x == 0 && threadIdx.x == 0) set_conds(ctl, 0u, 0u);
     const int nl = S->nlist;
-    const int ntiles = S->astart[nl];
-    const unsigned int nblk = ntiles < (int)gridDim.x ? (unsigned int)ntiles : gridDim.x;
+    const int nitems = S->bstart[nl];
+    const int spt = S->spt;
+    const unsigned int nblk = nitems < (int)gridDim.x ? (unsigned int)nitems : gridDim.x;
     if (blockIdx.x >= nblk) return;  // a running list is never empty here (an empty one halts)
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int k = find_start(S->astart, nl, t);
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x)
+    for (int q = 0; q < spt; ++q) {
+        const int k = find_start(S->bstart, nl, w);
         const int l = S->alist[k];
         const LatDesc &D = descs[l];
+        const int grp = (w - S->bstart[k]) * spt + q;
+        if (grp >= D.ntiles) break;  // uniform over the block
+        const int t = S->astart[k] + grp;
         const size_t vh = (size_t)D.g.vh;
-        const int i = (t - S->astart[k]) * kTile + threadIdx.x;
+        const int i = grp * kTile + threadIdx.x;
         double part = 0.0;
         if (i < D.g.vh) {
             const R alpha = (R)S->alpha[l];
@@ -442,7 +466,7 @@ struct BatchCtx {
     unsigned int *counter;
     int cap_tiles;
     // graph cache key and graph
-    int g_n, g_tiles, g_naik;
+    int g_n, g_tiles, g_naik, g_grid, g_spt;
     qex_prec g_inner;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -469,10 +493,50 @@ qex_status check_dslash_args(const qex_lattice *lat, qex_prec prec, const void *
 
 struct BatchLaunch {
     const BatchCtx *c;
-    int n, total_tiles, iter_grid;
+    int n, total_tiles, iter_grid, spt;
     qex_prec inner;
     bool naik, mixed;
 };
+
+// Work items of a batch with `spt` groups per item, and the iteration grid
+// of `per_sm` resident blocks per SM.
+static int batch_items(const std::vector<LatDesc> &d, int spt) {
+    int w = 0;
+    for (const LatDesc &D : d) w += (D.ntiles + spt - 1) / spt;
+    return w;
+}
+
+static int batch_grid(int items, int per_sm) {
+    const int resident = sm_count() * per_sm;
+    return items < resident ? items : resident;
+}
+
+// Set the groups per work item and rebuild the running list (one thread).
+__global__ void batch_relist_kernel(BatchScalars *S, const LatDesc *__restrict__ descs, int n, int spt) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        S->spt = spt;
+        compact_list(S, descs, n);
+    }
+}
+
+// Launch shapes chosen per (SM count, extents and boundary of every lattice
+// in order, inner precision, Naik), for the life of the process.
+struct BatchShape {
+    int per_sm, spt;
+};
+static std::map<std::string, BatchShape> g_batch_shapes;
+static std::mutex g_batch_mu;
+
+static std::string batch_key(int n, const qex_cg_item *items, qex_prec inner, bool naik) {
+    std::string k = "sm" + std::to_string(sm_count()) + " prec" + std::to_string((int)inner) + " naik" +
+                    std::to_string(naik ? 1 : 0);
+    for (int i = 0; i < n; ++i) {
+        const qex_lattice *l = items[i].lat;
+        k += " " + std::to_string(l->dims[0]) + "x" + std::to_string(l->dims[1]) + "x" + std::to_string(l->dims[2]) +
+             "x" + std::to_string(l->dims[3]) + (l->antiperiodic ? "a" : "p");
+    }
+    return k;
+}
 
 template <typename R, int FMT, bool NAIK>
 static void launch_iter_t(const BatchLaunch &b, int role, cudaStream_t s) {
@@ -492,18 +556,22 @@ static void launch_iter_n(const BatchLaunch &b, int role, cudaStream_t s) {
         launch_iter_t<R, FMT, false>(b, role, s);
 }
 
+static void launch_iter_role(const BatchLaunch &b, int role, cudaStream_t s) {
+    if (b.inner == QEX_F64)
+        launch_iter_n<double, 0>(b, role, s);
+    else if (b.inner == QEX_F32_R12)
+        launch_iter_n<float, 1>(b, role, s);
+    else if (b.inner == QEX_F32_R12H)
+        launch_iter_n<float, 2>(b, role, s);
+    else if (b.inner == QEX_F32_S16)
+        launch_iter_n<float, 3>(b, role, s);
+    else
+        launch_iter_n<float, 0>(b, role, s);
+}
+
 static qex_status enqueue_iteration(const BatchLaunch &b, const GraphCtl &ctl, cudaStream_t s) {
     for (int role = ROLE_K1; role <= ROLE_K2; ++role) {
-        if (b.inner == QEX_F64)
-            launch_iter_n<double, 0>(b, role, s);
-        else if (b.inner == QEX_F32_R12)
-            launch_iter_n<float, 1>(b, role, s);
-        else if (b.inner == QEX_F32_R12H)
-            launch_iter_n<float, 2>(b, role, s);
-        else if (b.inner == QEX_F32_S16)
-            launch_iter_n<float, 3>(b, role, s);
-        else
-            launch_iter_n<float, 0>(b, role, s);
+        launch_iter_role(b, role, s);
         QEX_CHECK_LAUNCH("batch_iter_dslash_kernel");
     }
     if (b.mixed)
@@ -613,14 +681,96 @@ static qex_status build_batch_graph(BatchCtx *c, const BatchLaunch &b) {
     }
     c->g_n = b.n;
     c->g_tiles = b.total_tiles;
+    c->g_grid = b.iter_grid;
+    c->g_spt = b.spt;
     c->g_naik = b.naik;
     c->g_inner = b.inner;
     return QEX_OK;
 }
 
+static bool batch_tuning_enabled() {
+    const char *e = getenv("QEX_TUNE");
+    return !(e && strcmp(e, "0") == 0);
+}
+
+// Time the two Dslash kernels of an iteration (both only overwrite scratch
+// and the per-lattice alpha, so repeating them changes nothing the loop then
+// computes) for every (blocks per SM, groups per item) candidate, each the
+// least of three short batches; keep the fastest.  The running list is left
+// built for the chosen items.
+static qex_status tune_batch(const BatchLaunch &b0, const std::vector<LatDesc> &descs, cudaStream_t s,
+                             BatchShape *best) {
+    cudaEvent_t e0, e1;
+    QEX_CUDA(cudaEventCreate(&e0));
+    QEX_CUDA(cudaEventCreate(&e1));
+    float best_us = 0.f;
+    *best = BatchShape{kBatchMinBlocks, 1};
+    qex_status st = QEX_OK;
+    set_count_launches(false);
+    for (int spt = 1; spt <= kMaxSpt && !st; spt *= 2)
+        for (int per_sm = 1; per_sm <= kBatchMinBlocks && !st; ++per_sm) {
+            BatchLaunch b = b0;
+            b.spt = spt;
+            b.iter_grid = batch_grid(batch_items(descs, spt), per_sm);
+            batch_relist_kernel<<<1, 32, 0, s>>>(const_cast<BatchScalars *>(b.c->S), b.c->descs, b.n, spt);
+            float cand = 0.f;
+            for (int rep = 0; rep < 4 && !st; ++rep) {  // rep 0 warms up
+                cudaEventRecord(e0, s);
+                for (int k = 0; k < 4; ++k)
+                    for (int role = ROLE_K1; role <= ROLE_K2; ++role) launch_iter_role(b, role, s);
+                cudaEventRecord(e1, s);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "timing a batch launch shape");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 || (rep > 1 && ms * 250.f < cand)) cand = ms * 250.f;  // us per iteration
+            }
+            if (!st && (best_us == 0.f || cand < best_us)) {
+                best_us = cand;
+                *best = BatchShape{per_sm, spt};
+            }
+        }
+    set_count_launches(true);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 }  // namespace qex
 
 using namespace qex;
+
+extern "C" qex_status qex_cg_batch_tune_info(const qex_lattice *lead, int *out) {
+    qex_status st;
+    if ((st = check_lattice(lead))) return st;
+    if (!out) {
+        set_error("out must not be NULL");
+        return QEX_ERR_ARG;
+    }
+    out[0] = lead->batch_shape[0] > 0 ? lead->batch_shape[0] : kBatchMinBlocks;
+    out[1] = lead->batch_shape[1] > 0 ? lead->batch_shape[1] : 1;
+    out[2] = lead->batch_shape[2];
+    return QEX_OK;
+}
+
+extern "C" qex_status qex_cg_batch_tune_set(const qex_lattice *lead, int blocks_per_sm, int groups_per_item) {
+    qex_status st;
+    if ((st = check_lattice(lead))) return st;
+    const bool unpin = blocks_per_sm == 0 && groups_per_item == 0;
+    if (!unpin && (blocks_per_sm < 1 || blocks_per_sm > kBatchMinBlocks ||
+                   (groups_per_item != 1 && groups_per_item != 2 && groups_per_item != 4))) {
+        set_error("need 1 <= blocks_per_sm <= %d and groups_per_item 1, 2 or 4 (0, 0 unpins)", kBatchMinBlocks);
+        return QEX_ERR_ARG;
+    }
+    qex_lattice *l = const_cast<qex_lattice *>(lead);
+    l->batch_pin[0] = unpin ? 0 : blocks_per_sm;
+    l->batch_pin[1] = unpin ? 0 : groups_per_item;
+    return QEX_OK;
+}
 
 extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inner, double tol, int maxiter,
                                    double delta, void *stream, qex_cg_stats *stats) {
@@ -730,21 +880,39 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
     b.c = c;
     b.n = n;
     b.total_tiles = total_tiles;
-    const int resident = sm_count() * kBatchMinBlocks;
-    b.iter_grid = total_tiles < resident ? total_tiles : resident;
     b.inner = inner;
     b.naik = naik;
     b.mixed = mixed;
-    if (use_graph && !(c->exec && c->g_n == n && c->g_tiles == total_tiles && c->g_naik == (int)naik &&
-                       c->g_inner == inner)) {
-        QEX_CUDA(cudaStreamSynchronize(s));
-        if ((st = build_batch_graph(c, b))) return st;
+    // launch shape: pinned on the lead lattice, from the process cache, the
+    // compiled defaults (QEX_TUNE=0), or measured after the first residual
+    const std::string key = batch_key(n, items, inner, naik);
+    int per_sm = kBatchMinBlocks, spt = 1, source = 0;
+    bool need_tune = false;
+    if (own->batch_pin[0] > 0) {
+        per_sm = own->batch_pin[0];
+        spt = own->batch_pin[1];
+        source = 4;
+    } else if (!batch_tuning_enabled()) {
+        source = 3;
+    } else {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        auto it = g_batch_shapes.find(key);
+        if (it != g_batch_shapes.end()) {
+            per_sm = it->second.per_sm;
+            spt = it->second.spt;
+            source = 2;
+        } else {
+            need_tune = true;
+        }
     }
+    b.spt = spt;
+    b.iter_grid = batch_grid(batch_items(descs, spt), per_sm);
 
     QEX_CUDA(cudaStreamSynchronize(s));  // the pinned slot is free
     BatchScalars *h = c->host;
     memset(h, 0, sizeof(*h));
     h->n = n;
+    h->spt = spt;
     h->tol2 = tol * tol;
     h->delta2 = mixed ? delta * delta : 0.0;
     h->maxiter = maxiter;
@@ -774,6 +942,30 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
     if ((st = enqueue_reliable_update(b, off, s)) || (st = fetch())) return st;
     for (int k = 0; k < n; ++k)  // zero sources: x = 0 exactly
         if (h->bb[k] == 0.0) QEX_CUDA(cudaMemsetAsync(items[k].x64, 0, (size_t)items[k].lat->vh * 48, s));
+    if (need_tune && !h->error && !h->halt) {
+        BatchShape best;
+        if ((st = tune_batch(b, descs, s, &best))) return st;
+        per_sm = best.per_sm;
+        spt = best.spt;
+        source = 1;
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        g_batch_shapes[key] = best;
+    }
+    if (spt != h->spt) {  // the list the first residual built is for another tile
+        batch_relist_kernel<<<1, 32, 0, s>>>(c->S, c->descs, n, spt);
+        QEX_CHECK_LAUNCH("batch_relist_kernel");
+    }
+    b.spt = spt;
+    b.iter_grid = batch_grid(batch_items(descs, spt), per_sm);
+    own->batch_shape[0] = per_sm;
+    own->batch_shape[1] = spt;
+    own->batch_shape[2] = source;
+    if (use_graph && !h->error && !h->halt &&
+        !(c->exec && c->g_n == n && c->g_tiles == total_tiles && c->g_naik == (int)naik && c->g_inner == inner &&
+          c->g_grid == b.iter_grid && c->g_spt == spt)) {
+        QEX_CUDA(cudaStreamSynchronize(s));
+        if ((st = build_batch_graph(c, b))) return st;
+    }
     if (!h->error && !h->halt) {
         if (use_graph) {
             QEX_CUDA(cudaGraphLaunch(c->exec, s));

@@ -206,6 +206,9 @@ qex_status qex_lattice_destroy(qex_lattice *lat) {
     if (lat->host_work) cudaFree(lat->host_work);
     if (lat->cg_graph) free_cg_graph(lat->cg_graph);
     if (lat->batch_ctx) free_batch_ctx(lat->batch_ctx);
+    if (lat->copy_stream) cudaStreamDestroy(lat->copy_stream);
+    for (cudaEvent_t e : lat->slab_ev)
+        if (e) cudaEventDestroy(e);
     if (lat->ev0) cudaEventDestroy(lat->ev0);
     if (lat->ev1) cudaEventDestroy(lat->ev1);
     delete lat;

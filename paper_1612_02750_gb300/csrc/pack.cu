@@ -1,5 +1,7 @@
 // pack.cu -- conversions between the canonical lexicographic layouts and the
 // internal even-odd structure-of-arrays layouts, and FP64 <-> FP32 copies.
+#include <type_traits>
+
 #include "qex_kernels.cuh"
 
 namespace qex {
@@ -227,6 +229,24 @@ __global__ void pack_links_kernel(Geom g, const double *__restrict__ lex, R out)
     put_link(out, g.vh, blk, i, m);
 }
 
+// The links of the internal indices [i0, i1) of both parities (a range of
+// t-slices), written in FP64 and, unless R is void*, also in a second format:
+// each canonical link is read once for both.
+template <typename R>
+__global__ void pack_links_range_kernel(Geom g, const double *__restrict__ lex, double *out64, R out2, int i0,
+                                        int i1) {
+    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= i1) return;
+    const int blk = blockIdx.y, p = blk >> 2, mu = blk & 3;
+    const Site s = site_of(g, p, i);
+    const double *src = lex + ((size_t)s.lex * 4 + mu) * 18;
+    double m[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) m[k] = src[k];
+    put_link(out64, g.vh, blk, i, m);
+    if constexpr (!std::is_same<R, void *>::value) put_link(out2, g.vh, blk, i, m);
+}
+
 template <typename R>
 __global__ void unpack_links_kernel(Geom g, R in, double *__restrict__ lex) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -306,6 +326,31 @@ static void convert_links_to(qex_prec to, int vh, RI in, void *out, dim3 grid, c
         convert_links_kernel<RI, R12H><<<grid, kBlock, 0, s>>>(vh, in, R12H{(float *)out});
     else
         convert_links_kernel<RI, S16><<<grid, kBlock, 0, s>>>(vh, in, S16{(float *)out});
+}
+
+// Pack the canonical links of internal indices [i0, i1) (both parities) into
+// out64 (FP64) and, when out2 is given, into out2 in format `second` too.
+qex_status launch_pack_links_range(qex_lattice *lat, const double *lex, void *out64, qex_prec second, void *out2,
+                                   int i0, int i1, cudaStream_t s) {
+    if (i1 <= i0) return QEX_OK;
+    dim3 grid(blocks_for(i1 - i0), 8);
+    double *o = (double *)out64;
+    if (!out2)
+        pack_links_range_kernel<void *><<<grid, kBlock, 0, s>>>(lat->geom, lex, o, nullptr, i0, i1);
+    else if (second == QEX_F32)
+        pack_links_range_kernel<float *><<<grid, kBlock, 0, s>>>(lat->geom, lex, o, (float *)out2, i0, i1);
+    else if (second == QEX_F32_R12)
+        pack_links_range_kernel<R12><<<grid, kBlock, 0, s>>>(lat->geom, lex, o, R12{(float *)out2}, i0, i1);
+    else if (second == QEX_F32_R12H)
+        pack_links_range_kernel<R12H><<<grid, kBlock, 0, s>>>(lat->geom, lex, o, R12H{(float *)out2}, i0, i1);
+    else if (second == QEX_F32_S16)
+        pack_links_range_kernel<S16><<<grid, kBlock, 0, s>>>(lat->geom, lex, o, S16{(float *)out2}, i0, i1);
+    else {
+        set_error("internal: no second link format %d", (int)second);
+        return QEX_ERR_ARG;
+    }
+    QEX_CHECK_LAUNCH("pack_links_range_kernel");
+    return QEX_OK;
 }
 
 }  // namespace qex

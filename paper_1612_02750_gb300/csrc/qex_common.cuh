@@ -525,6 +525,8 @@ struct qex_lattice {
     size_t work_bytes;
     void *host_work;           // staging of qex_cg_host
     size_t host_work_bytes;
+    cudaStream_t copy_stream;  // qex_cg_host: host-to-device copies of the link slabs
+    cudaEvent_t slab_ev[9];    // ... one event per slab, and one ordering event
     void *cg_graph;            // cached CUDA graph of the last CG solve
     void *batch_ctx;           // scratch of qex_cg_batch calls led by this lattice
     cudaEvent_t ev0, ev1;
@@ -534,6 +536,8 @@ struct qex_lattice {
     int blas_per_sm;           // 0: QEX_BLAS_BLOCKS_PER_SM
     int pdl;                   // CG kernels launch with programmatic dependent launch (set by qex_cg)
     int fused_blocks;          // grid of the last fused CG launch
+    int batch_pin[2];          // qex_cg_batch_tune_set: blocks per SM, groups per item (0: not pinned)
+    int batch_shape[3];        // shape of the last batch led by this lattice: blocks per SM, groups per item, source
 };
 
 namespace qex {
@@ -552,6 +556,7 @@ qex_status check_prec(qex_prec prec);
 inline bool is_f64(qex_prec p) { return p == QEX_F64; }
 
 constexpr int kBlock = 256;  // threads per block of the site kernels
+constexpr int kHostSlabs = 8;  // t-slabs of a link set in qex_cg_host (lattice::slab_ev holds one more)
 
 // Dslash launch shape: threads per block and the minimum resident blocks per
 // SM handed to __launch_bounds__ (which caps registers per thread).

@@ -80,18 +80,76 @@ def test_batch_matches_oracle_and_single(q, oracle_mod, inner, naik):
         assert_close(x[ev], xr[ev], 1e-7, ("x against the oracle's 1e-13 solve", k))
 
 
-def test_batch_multi_lattice_workload_small(q, oracle_mod):
-    """The four smallest lattices of the multi-lattice workload (8^4, 12^4,
-    16^4, 16^3 x 32, Haar links, masses m_k = 0.005 * 20^(k/7)) in one batch
-    with 16-bit inner links: all converge to an oracle-checked 1e-10."""
-    dims_list = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32)]
-    masses = [0.005 * 20 ** (k / 7) for k in range(4)]
+@pytest.mark.slow
+def test_batch_multi_lattice_workload_full(q, oracle_mod):
+    """The multi-lattice workload in full: eight lattices 8^4, 12^4, 16^4,
+    16^3 x 32, 20^4, 24^4, 24^3 x 48, 32^4 (Haar links, seed 4 + 10k, masses
+    m_k = 0.005 * 20^(k/7) in that order) in one batch with 16-bit inner links
+    and the tuned launch shape: every lattice converges and the oracle
+    recomputes each true residual <= 1.05e-10."""
+    dims_list = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (20, 20, 20, 20),
+                 (24, 24, 24, 24), (24, 24, 24, 48), (32, 32, 32, 32)]
+    masses = [0.005 * 20 ** (k / 7) for k in range(8)]
     probs = [_problem(q, d, m, 4 + 10 * k, False, "f32r12h") for k, (d, m) in enumerate(zip(dims_list, masses))]
-    st, stats = q.qex_cg_batch([p[0] for p in probs], "f32r12h", tol=1e-10, maxiter=200000, delta=0.1)
+    st, stats = q.qex_cg_batch([p[0] for p in probs], "f32r12h", tol=1e-10, maxiter=400000, delta=0.1)
     assert st == 0 and all(s["converged"] for s in stats), stats
+    shape = q.qex_cg_batch_tune_info(probs[0][0]["lat"])
+    assert shape["source"] in ("measured", "cache", "disabled"), shape
     for k, (item, u, w, b) in enumerate(probs):
         x = q.qex_unpack_field(item["lat"], "f64", 0, item["x64"]).cpu().numpy()
-        assert oracle_mod.true_residual(dims_list[k], u, b, x, masses[k]) <= 1.05e-10
+        assert oracle_mod.true_residual(dims_list[k], u, b, x, masses[k]) <= 1.05e-10, k
+
+
+@pytest.mark.parametrize("inner,naik", [("f32r12h", True), ("f64", False)])
+def test_batch_shapes_give_identical_bits(q, oracle_mod, inner, naik):
+    """Every (blocks per SM, groups per work item) shape runs the same
+    per-site arithmetic and the same per-256-site-group reductions: pinned
+    shapes (1, 1), (3, 2), (2, 4) and the autotuner's choice give the same
+    iteration counts and bit-identical solutions, which meet the oracle."""
+    import torch
+
+    runs = []
+    for pin in ((1, 1), (3, 2), (2, 4), None):
+        probs = [_problem(q, d, m, 110 + k, naik, inner) for k, (d, m) in enumerate(SPECS)]
+        lead = probs[0][0]["lat"]
+        if pin:
+            q.qex_cg_batch_tune_set(lead, *pin)
+        st, stats = q.qex_cg_batch([p[0] for p in probs], inner, tol=1e-10, delta=0.1)
+        assert st == 0 and all(s["converged"] for s in stats), (pin, stats)
+        info = q.qex_cg_batch_tune_info(lead)
+        if pin:
+            assert (info["blocks_per_sm"], info["groups_per_item"], info["source"]) == (pin[0], pin[1], "set")
+        else:
+            assert info["source"] in ("measured", "cache", "disabled")
+        runs.append(([s["iters"] for s in stats], [p[0]["x64"].clone() for p in probs], probs))
+    for its, xs, _ in runs[1:]:
+        assert its == runs[0][0]
+        for a, b in zip(xs, runs[0][1]):
+            assert torch.equal(a, b)
+    for k, (item, u, w, b) in enumerate(runs[0][2]):
+        x = q.qex_unpack_field(item["lat"], "f64", 0, runs[0][1][k]).cpu().numpy()
+        assert oracle_mod.true_residual(SPECS[k][0], u, b, x, item["mass"], w, item["c_naik"]) <= 1.05e-10
+
+
+def test_batch_tuner_measures_once_per_key(q, monkeypatch):
+    """A set of extents the process has not seen: the first batch measures
+    the launch shape, the next batch with the same extents takes it from the
+    process cache; a pin is reported as set and (0, 0) removes it."""
+    monkeypatch.delenv("QEX_TUNE", raising=False)
+    specs = [((4, 4, 6, 10), 0.2), ((6, 6, 4, 8), 0.15)]  # extents no other test batches
+    sources = []
+    for _ in range(2):
+        probs = [_problem(q, d, m, 120 + k, False, "f32r12h") for k, (d, m) in enumerate(specs)]
+        st, _ = q.qex_cg_batch([p[0] for p in probs], "f32r12h", tol=1e-10, delta=0.1)
+        assert st == 0
+        sources.append(q.qex_cg_batch_tune_info(probs[0][0]["lat"])["source"])
+    assert sources == ["measured", "cache"]
+    with pytest.raises(q.QexError) as e:
+        q.qex_cg_batch_tune_set(probs[0][0]["lat"], 4, 1)
+    assert e.value.status == 1
+    with pytest.raises(q.QexError):
+        q.qex_cg_batch_tune_set(probs[0][0]["lat"], 2, 3)
+    q.qex_cg_batch_tune_set(probs[0][0]["lat"], 0, 0)
 
 
 def test_batch_errors(q):

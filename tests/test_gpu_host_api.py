@@ -26,14 +26,15 @@ def q():
 
 
 @pytest.mark.parametrize("naik", [False, True])
-@pytest.mark.parametrize("inner", ["f64", "f32r12h"])
-def test_cg_host_matches_device_solve(q, oracle_mod, inner, naik):
-    """Same kernels on the same bits: the host-buffer solve returns the device
-    solve's iterate exactly, with zeros on the odd sites, and meets the
-    oracle's true residual."""
+@pytest.mark.parametrize("inner", ["f64", "f32r12h", "f32s16"])
+@pytest.mark.parametrize("dims", [(8, 4, 6, 8), (6, 4, 4, 10)])
+def test_cg_host_matches_device_solve(q, oracle_mod, inner, naik, dims):
+    """Same kernels on the same bits: the host-buffer solve (links copied and
+    packed in t-slabs: 8 slabs of one slice, or 8 slabs of one or two slices
+    for Lt = 10) returns the device solve's iterate exactly, with zeros on the
+    odd sites, and meets the oracle's true residual."""
     import torch
 
-    dims = (8, 4, 6, 8)
     m = 0.1
     S = Setup(q, dims, naik, seed=41)
     b = S.psi.copy()
