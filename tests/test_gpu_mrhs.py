@@ -179,3 +179,36 @@ def test_cg_mrhs_errors(q):
     assert e.value.status == 1
     st, stats = q.qex_cg_mrhs(lat, "f64", fat, None, None, None, 0.0, 0.1, 2, B, X)  # zero sources
     assert st == 0 and all(s["converged"] for s in stats) and not X.any()
+
+
+@pytest.mark.slow
+def test_cg_mrhs_workload_24x24x24x24_16_sources(q, oracle_mod):
+    """The multi-RHS workload in full: 24^4, Haar links (seed 4), 16 Gaussian
+    even-site sources, m = 0.05, one batched mixed-precision solve (two-row
+    FP32 inner links, FP64 reliable updates, delta = 0.01) to 1e-10: every
+    source converges and the oracle recomputes each true residual."""
+    import torch
+
+    dims, nrhs, seed, m = (24, 24, 24, 24), 16, 4, 0.05
+    st = fg.rng_streams(seed)
+    u = fg.random_links(dims, "haar", st["links"])
+    ev = fg.even_mask(dims)
+    srcs = []
+    for _ in range(nrhs):
+        b = fg.gaussian_field(st["source"], dims)
+        b[~ev] = 0
+        srcs.append(b)
+    lat = q.Lattice(dims)
+    fat64 = q.qex_pack_links(lat, "f64", dev(u))
+    fatr = q.qex_convert_links(lat, "f64", fat64, "f32r12")
+    B = torch_cat(q, [q.qex_pack_field(lat, "f64", 0, dev(b)) for b in srcs])
+    X = torch.zeros_like(B)
+    status, stats = q.qex_cg_mrhs(lat, "f32r12", fat64, None, fatr, None, 0.0, m, nrhs, B, X, tol=1e-10,
+                                  delta=0.01)
+    assert status == 0 and all(s["converged"] for s in stats), stats
+    n = q.qex_field_bytes(lat, "f64") // 8
+    for r, b in enumerate(srcs):
+        x = q.qex_unpack_field(lat, "f64", 0, X[r * n:(r + 1) * n].contiguous()).cpu().numpy()
+        tr = oracle_mod.true_residual(dims, u, b, x, m)
+        assert tr <= 1.05e-10, (r, tr)
+        assert stats[r]["true_rel_resid"] == pytest.approx(tr, rel=1e-3)

@@ -481,8 +481,11 @@ def test_full_size_64_naik_sampled_sites(q, oracle_mod):
     both parities and four formats (FP64, FP32, two-row FP32 fat with FP32
     long links, 16-bit two-row fat with 16-bit scaled long links) on 4096
     sampled output sites
-    against the oracle's per-site sum, and anti-hermiticity
-    <chi, D_eo psi> = -<D_oe chi, psi> over the whole lattice in FP64."""
+    against the oracle's per-site sum, anti-hermiticity
+    <chi, D_eo psi> = -<D_oe chi, psi> over the whole lattice in FP64, and the
+    workload's mixed-precision solve (m = 0.005, about 34,000 iterations and
+    100 s on a GB300) to a true residual of 1e-10 that the oracle
+    recomputes."""
     import torch
 
     wl = fg.workload("cfg64naik")
@@ -519,3 +522,18 @@ def test_full_size_64_naik_sampled_sites(q, oracle_mod):
     lhs = host(q.qex_dot(lat, "f64", chi_e, d_eo_psi))
     rhs = host(q.qex_dot(lat, "f64", d_oe_chi, psi_o))
     assert abs(complex(*lhs) + complex(*rhs)) <= 1e-12 * abs(complex(*lhs))
+    del d_eo_psi, d_oe_chi, psi_o, links
+    torch.cuda.empty_cache()
+    # the workload's solve: mixed-precision CG (two-row FP32 fat and FP32 long links inside, FP64
+    # reliable updates, delta = 0.01) from x = 0 to a true residual of 1e-10, m = 0.005; the oracle
+    # recomputes the true residual of the returned x
+    fat_i = q.qex_convert_links(lat, "f64", fat64, "f32r12")
+    lng_i = q.qex_convert_links(lat, "f64", lng64, q.qex_long_links_prec("f32r12"))
+    x = torch.zeros_like(chi_e)
+    st, stats = q.qex_cg(lat, "f32r12", fat64, lng64, fat_i, lng_i, C3, wl["mass"], chi_e, x, tol=1e-10,
+                         maxiter=100000, delta=0.01, check=False)
+    assert st == 0 and stats["converged"], stats
+    xf = host(q.qex_unpack_field(lat, "f64", 0, x))
+    tr = oracle_mod.true_residual(dims, u, b, xf, wl["mass"], w, C3)
+    assert tr <= 1.05e-10, (stats, tr)
+    assert stats["true_rel_resid"] == pytest.approx(tr, rel=1e-3)
