@@ -23,6 +23,7 @@ run every other test first.
 """
 
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -167,13 +168,21 @@ def test_static_normal_op_allocates_nothing(q, prec):
     out = q.empty_field(lat, prec)
     assert _call_static(q, lat, prec, fat, lng, C3, 0.1, inp, out) == 0, q.qex_last_error()
     torch.cuda.synchronize()
-    alloc0 = torch.cuda.memory_allocated()
-    free0, _ = torch.cuda.mem_get_info()
-    for mass in (0.2, 0.05):
-        assert _call_static(q, lat, prec, fat, lng, C3, mass, inp, out) == 0, q.qex_last_error()
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
-    assert torch.cuda.memory_allocated() == alloc0
+    # no Python garbage collection in between: it could free an earlier test's tensor and move
+    # torch's count for a reason that has nothing to do with the calls
+    gc.collect()
+    gc.disable()
+    try:
+        alloc0 = torch.cuda.memory_allocated()
+        free0, _ = torch.cuda.mem_get_info()
+        for mass in (0.2, 0.05):
+            assert _call_static(q, lat, prec, fat, lng, C3, mass, inp, out) == 0, q.qex_last_error()
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        alloc1 = torch.cuda.memory_allocated()
+    finally:
+        gc.enable()
+    assert alloc1 == alloc0
     assert free1 == free0
 
 
