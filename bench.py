@@ -410,7 +410,14 @@ def run_native(args):
 
     dslash = {p: {"ms": round(t, 5), "GB/s": round(gbs(p), 1), "frac": round(gbs(p) / peak, 4),
                   "GFLOP/s": round(FLOP_NN * vh / (t * 1e-3) / 1e9, 1)} for p, t in times.items()}
-    dslash["f64"]["bound"] = "fp64 alu (see fp64_fma_peak)"
+    rates = q.qex_fma_rates()
+    f64_flops = 2 * 288 * vh / (times["f64"] * 1e-3) / 1e9  # 288 FP64 FMAs issued per site
+    dslash["f64"]["bound"] = "alu"
+    dslash["f64"]["alu"] = {"achieved_gflops": round(f64_flops, 1), "peak_gflops": round(rates["fp64_gflops"], 1),
+                            "frac": round(f64_flops / rates["fp64_gflops"], 4), "unit": "GFLOP/s",
+                            "peak_source": "qex_fma_rates: FP64 FMA chains timed on this GPU in this run",
+                            "fma_per_site": 288}
+    dslash["fp32_fma_gflops"] = round(rates["fp32_gflops"], 1)
     dslash["timing"] = "D_oe alone, cold L2 (read of 2x L2 before each launch), 40 launches, CUDA events"
     dslash["traffic_f32r12h"] = ncu_traffic("dslash_f32r12h_nn_32^4")
 

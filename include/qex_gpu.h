@@ -508,6 +508,16 @@ qex_status qex_tune_info(const qex_lattice *lat, qex_prec prec, int naik, int *o
  * Paper: no counterpart. */
 qex_status qex_tune_set(const qex_lattice *lat, qex_prec prec, int naik, const int *in);
 
+/* Measured fused multiply-add rates of the current GPU, in GFLOP/s (2 flops
+ * per FMA): *fp64_gflops (double) and *fp32_gflops (float, scalar FMA), from
+ * fixed-trip FMA chains over several resident waves, timed with CUDA events
+ * on `stream` (best of five bursts of a few ms; allocates and frees 512 KB of scratch;
+ * synchronises the stream).  The FP64 rate bounds the FP64 Dslash on a GPU
+ * whose FP64 units are few (GB300: about 1.2 TFLOP/s, 288 FP64 FMAs per site).
+ * Errors: QEX_ERR_ARG (NULL), QEX_ERR_CUDA.
+ * Paper: no counterpart (a measurement of the hardware). */
+qex_status qex_fma_rates(double *fp64_gflops, double *fp32_gflops, void *stream);
+
 /* Number of kernels this library has launched in the calling process so far
  * (monotone counter, for accounting of the kernels in a timed region).
  * Paper: no counterpart.

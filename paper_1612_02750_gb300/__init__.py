@@ -106,6 +106,7 @@ def load():
         "qex_tune": (i, [vp, i, vp, vp, vp]),
         "qex_tune_info": (i, [vp, i, i, ip]),
         "qex_tune_set": (i, [vp, i, i, ip]),
+        "qex_fma_rates": (i, [ctypes.POINTER(d), ctypes.POINTER(d), vp]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -126,7 +127,7 @@ def exported_symbols():
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
             "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch",
             "qex_cg_batch_tune_info", "qex_cg_batch_tune_set", "qex_long_links_prec", "qex_tune", "qex_tune_info",
-            "qex_tune_set", "qex_launch_count", "qex_last_error", "qex_version"]
+            "qex_tune_set", "qex_fma_rates", "qex_launch_count", "qex_last_error", "qex_version"]
 
 
 def _check(status: int):
@@ -498,6 +499,13 @@ def qex_tune_set(lat: Lattice, prec, naik: bool = False, dslash_block: int = 256
     fields)."""
     arr = (ctypes.c_int * 5)(dslash_block, reduce_block, reduce_blocks_per_sm, blas_blocks_per_sm, dslash_waves)
     _check(load().qex_tune_set(lat.handle, _prec(prec), 1 if naik else 0, arr))
+
+
+def qex_fma_rates(stream=None) -> dict:
+    """Measured FP64 and FP32 FMA rates of the current GPU (GFLOP/s)."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check(load().qex_fma_rates(ctypes.byref(f64), ctypes.byref(f32), _stream(stream)))
+    return {"fp64_gflops": f64.value, "fp32_gflops": f32.value}
 
 
 def qex_launch_count() -> int:

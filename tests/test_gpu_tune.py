@@ -189,3 +189,14 @@ def test_tune_errors(q):
         q.qex_tune(lat, "f64", fat, fat)  # Naik with an extent of 2
     assert e.value.status == 2
     assert q.qex_tune_info(lat, "f64")["source"] == "default"
+
+
+def test_fma_rates_are_measured(q):
+    """qex_fma_rates times FP64 and FP32 FMA chains on this GPU: both rates
+    are positive and finite, and FP32 is the faster (on a GB300 FP64 is about
+    1/60 of it)."""
+    import math
+
+    r = q.qex_fma_rates()
+    assert all(math.isfinite(v) and v > 0 for v in r.values()), r
+    assert r["fp32_gflops"] > 4 * r["fp64_gflops"], r
