@@ -697,7 +697,7 @@ static bool batch_tuning_enabled() {
 // and the per-lattice alpha, so repeating them changes nothing the loop then
 // computes) for every (blocks per SM, groups per item) candidate, each the
 // least of three short batches; keep the fastest.  The running list is left
-// built for the chosen items.
+// built for the last candidate's items: the caller rebuilds it.
 static qex_status tune_batch(const BatchLaunch &b0, const std::vector<LatDesc> &descs, cudaStream_t s,
                              BatchShape *best) {
     cudaEvent_t e0, e1;
@@ -942,16 +942,18 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
     if ((st = enqueue_reliable_update(b, off, s)) || (st = fetch())) return st;
     for (int k = 0; k < n; ++k)  // zero sources: x = 0 exactly
         if (h->bb[k] == 0.0) QEX_CUDA(cudaMemsetAsync(items[k].x64, 0, (size_t)items[k].lat->vh * 48, s));
+    bool relist = spt != h->spt;  // the list the first residual built is for another item size
     if (need_tune && !h->error && !h->halt) {
         BatchShape best;
         if ((st = tune_batch(b, descs, s, &best))) return st;
         per_sm = best.per_sm;
         spt = best.spt;
         source = 1;
+        relist = true;  // the timing left the list built for its last candidate
         std::lock_guard<std::mutex> lk(g_batch_mu);
         g_batch_shapes[key] = best;
     }
-    if (spt != h->spt) {  // the list the first residual built is for another tile
+    if (relist) {
         batch_relist_kernel<<<1, 32, 0, s>>>(c->S, c->descs, n, spt);
         QEX_CHECK_LAUNCH("batch_relist_kernel");
     }
