@@ -675,9 +675,8 @@ def run_sweep(args):
         del u, w
         torch.cuda.empty_cache()
         bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
-        # inner formats: FP32 two-row fat + FP32 long links, and 16-bit two-row fat + 16-bit scaled long
-        # links (Haar links at m = 0.005: delta 0.1 for the 16-bit inner solve, as on the 16^4 Haar study)
-        for inner, delta in (("f32r12", DELTA), ("f32r12h", 0.1)):
+        # inner formats: FP32 two-row fat + FP32 long links, and 16-bit two-row fat + 16-bit scaled long links
+        for inner, delta in (("f32r12", DELTA), ("f32r12h", DELTA)):
             fati = q.qex_convert_links(lat, "f64", fat64, inner)
             lngi = q.qex_convert_links(lat, "f64", lng64, q.qex_long_links_prec(inner))
             x = torch.zeros_like(bh)
@@ -795,7 +794,7 @@ def run_batch(args):
         bh = q.qex_pack_field(lat, "f64", 0, torch.from_numpy(b).cuda())
         items.append({"lat": lat, "fat64": fat64, "fat32": q.qex_convert_links(lat, "f64", fat64, INNER),
                       "mass": 0.005 * 20 ** (k / 7), "b64": bh, "x64": torch.zeros_like(bh)})
-    delta = 0.1  # Haar links: the robust setting for 16-bit inner links
+    delta = DELTA
     q.qex_cg_batch(items, INNER, tol=TOL, maxiter=400000, delta=delta)  # warm-up (builds scratch)
     for it in items:  # warm-up of the single solves (launch-shape tuning, graph capture)
         x = torch.zeros_like(it["b64"])

@@ -303,6 +303,11 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  *   whenever the iterated residual norm drops below delta times its maximum
  *   since the last update (or meets tol), the FP64 solution is updated and the
  *   residual is recomputed in FP64 with fat64/lng64 (reliable update).
+ *   A reliable update also follows any 100 inner iterations without one with
+ *   16-bit links (QEX_F32_R12H, QEX_F32_S16) and any 500 with FP32 links: over
+ *   longer cycles (small mass) the inner recursion residual drifts away from
+ *   the true one and the solve stalls.  The environment variable
+ *   QEX_RU_CYCLE = n sets another bound (0: none), read at each solve.
  * b64, x64: F64 even half fields; x64 holds the initial guess on entry and the
  *   solution on return.  lng64/lng32 NULL = no Naik term.
  * Synchronises the stream before returning (fills stats, may be NULL).
@@ -374,7 +379,8 @@ qex_status qex_force(const qex_lattice *lat, const void *fat64, const void *lng6
  * x64 holds the initial guesses and receives the solutions.  The solves
  * iterate in lockstep; each stops (is frozen) when its own FP64 true residual
  * meets tol; a reliable update requested by any running one is done for all
- * running ones.  stats (may be NULL) receives nrhs entries.  Synchronises the
+ * running ones (the cycle bound of qex_cg counts lockstep iterations).  stats
+ * (may be NULL) receives nrhs entries.  Synchronises the
  * stream.  Errors as qex_cg (QEX_ERR_NOT_CONVERGED if any right-hand side did
  * not converge).
  * Paper: extends the one-right-hand-side solver of Sec. 4 and Fig. 1.
@@ -389,7 +395,7 @@ qex_status qex_cg_mrhs(const qex_lattice *lat, qex_prec inner, const void *fat64
 /* One problem of a batched solve: its own lattice object (not shared with
  * another item), links, mass, source and solution.  fat64/lng64: F64 link
  * sets; fat32/lng32: the inner-precision copies (fat32 in the `inner` link
- * format, lng32 in QEX_F32) when inner != QEX_F64; lng64 NULL = no Naik
+ * format, lng32 in qex_long_links_prec(inner)) when inner != QEX_F64; lng64 NULL = no Naik
  * term (all items of a batch agree).  b64, x64: F64 even half fields, x64
  * holding the initial guess. */
 typedef struct {
@@ -406,7 +412,8 @@ typedef struct {
  * masses): every kernel of an iteration is one launch over a work list of
  * (lattice, tile) items of all running lattices, so small lattices share
  * the GPU (tile size and grid: qex_cg_batch_tune_info).  Each lattice has its own alpha, beta, residual norms,
- * reliable updates and FP64 true-residual stop (tol, maxiter and delta are
+ * reliable updates (with the cycle bound of qex_cg, counted in its own
+ * iterations) and FP64 true-residual stop (tol, maxiter and delta are
  * common); the lattices iterate in lockstep and a converged one stops.  The
  * scratch of the batch (descriptors, scalars, per-tile partials) is owned by
  * items[0].lat; the CG vectors of each item live in its own lattice's work

@@ -105,7 +105,8 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf
         return;
     }
     if (rr_new > S->rmax2) S->rmax2 = rr_new;
-    if (rr_new <= S->stop2 || rr_new < S->delta2 * S->rmax2 || S->iters >= S->maxiter) {
+    const bool long_cycle = S->max_cycle > 0 && S->iters - S->ru_iter0 >= S->max_cycle;
+    if (rr_new <= S->stop2 || rr_new < S->delta2 * S->rmax2 || S->iters >= S->maxiter || long_cycle) {
         // FP64 true residual next (reliable update / convergence check); rr
         // keeps the previous value so that beta is formed from the true one
         S->need_ru = 1;

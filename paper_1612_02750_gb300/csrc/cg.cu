@@ -417,6 +417,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     memset(&init, 0, sizeof(init));
     init.tol2 = tol * tol;
     init.delta2 = mixed ? delta * delta : 0.0;
+    init.max_cycle = ru_max_cycle(inner);
     init.maxiter = maxiter;
     CgScalars *h0 = lat->scalars_host, *h1 = lat->scalars_host2;
     QEX_CUDA(cudaStreamSynchronize(cst));  // the pinned slots are free

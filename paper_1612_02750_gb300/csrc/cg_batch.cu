@@ -56,8 +56,10 @@ struct BatchScalars {
     int alist[kMaxRhs];       // running lattices, in lattice order
     int astart[kMaxRhs + 1];  // their first group in the compacted group list; astart[nlist] = groups
     int bstart[kMaxRhs + 1];  // their first work item (spt groups) in the compacted list
+    int ru_iter0[kMaxRhs];    // iters[l] at lattice l's last reliable update
     int spt;                  // groups per work item
     int nlist;
+    int max_cycle;            // > 0: a reliable update also follows max_cycle iterations without one
     double tol2, delta2;
     int n, iter, maxiter, halt, error, any_need, nactive, reliable_updates, trips;
 };
@@ -290,7 +292,8 @@ batch_update_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *
             continue;
         }
         if (v > S->rmax2[l]) S->rmax2[l] = v;
-        if (v <= S->stop2[l] || v < S->delta2 * S->rmax2[l] || S->iter >= S->maxiter) {
+        if (v <= S->stop2[l] || v < S->delta2 * S->rmax2[l] || S->iter >= S->maxiter ||
+            (S->max_cycle > 0 && S->iters[l] - S->ru_iter0[l] >= S->max_cycle)) {
             S->need[l] = 1;  // rr keeps its old value: beta comes from the true residual
             any = 1;
         } else {
@@ -352,6 +355,7 @@ batch_ru_dslash_kernel(const LatDesc *__restrict__ descs, int n, BatchScalars *S
             if (!need[k] || !S->need[k]) continue;
             const double v = tot[k];
             S->need[k] = 0;
+            S->ru_iter0[k] = S->iters[k];
             S->true_rr[k] = v;
             if (!isfinite(v)) {
                 S->error = 1;
@@ -915,6 +919,7 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
     h->spt = spt;
     h->tol2 = tol * tol;
     h->delta2 = mixed ? delta * delta : 0.0;
+    h->max_cycle = ru_max_cycle(inner);
     h->maxiter = maxiter;
     for (int k = 0; k < n; ++k) h->active[k] = 1;
     cudaEvent_t t0, t1;

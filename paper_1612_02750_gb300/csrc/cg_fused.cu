@@ -261,7 +261,8 @@ __device__ __forceinline__ void cg_fused_body(const FusedArgs<R> &A) {
                     st.error = 1;
                 } else {
                     if (rr_new > st.rmax2) st.rmax2 = rr_new;
-                    if (rr_new <= S->stop2 || rr_new < S->delta2 * st.rmax2 || st.iters >= S->maxiter) {
+                    const bool long_cycle = S->max_cycle > 0 && st.iters - S->ru_iter0 >= S->max_cycle;
+                    if (rr_new <= S->stop2 || rr_new < S->delta2 * st.rmax2 || st.iters >= S->maxiter || long_cycle) {
                         st.need_ru = 1;  // rr keeps its value: beta then comes from the true residual
                     } else {
                         st.beta = rr_new / st.rr;

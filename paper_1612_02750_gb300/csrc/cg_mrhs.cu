@@ -94,7 +94,8 @@ update_xr_mrhs_kernel(int vh, int nrhs, R *__restrict__ x, R *__restrict__ r, R 
         *counter = 0u;
         if (S->error) {
             S->halt = 1;
-        } else if (any_ru || S->iter >= S->maxiter) {
+        } else if (any_ru || S->iter >= S->maxiter ||
+                   (S->max_cycle > 0 && S->iter - S->ru_iter0 >= S->max_cycle)) {
             S->need_ru = 1;
             S->halt = 1;
         } else {
@@ -260,6 +261,7 @@ extern "C" qex_status qex_cg_mrhs(const qex_lattice *latc, qex_prec inner, const
     init.nrhs = nrhs;
     init.tol2 = tol * tol;
     init.delta2 = mixed ? delta * delta : 0.0;
+    init.max_cycle = ru_max_cycle(inner);
     init.maxiter = maxiter;
     for (int q = 0; q < nrhs; ++q) init.active[q] = 1;
     MrhsScalars *host = nullptr;

@@ -9,7 +9,6 @@
 // antiperiodic time boundary are computed from the site coordinates; no phase
 // is folded into the links.
 #include <type_traits>
-
 #include "qex_dslash_site.cuh"
 #include "qex_kernels.cuh"
 
@@ -180,6 +179,7 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
                 S->halt = 1;
                 return;
             }
+            S->ru_iter0 = S->iters;
             S->beta = S->rr > 0.0 ? tot / S->rr : 0.0;
             S->rr = tot;
             S->rmax2 = tot;

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kMrhsBlock, kMrhsMinBlocks) dslash_mrhs_kernel
                 for (int r = 0; r < P.nrhs; ++r) n += S->active[r];
                 S->nactive = n;
                 S->need_ru = 0;
+                S->ru_iter0 = S->iter;
                 S->reliable_updates += 1;
                 S->halt = (n == 0 || S->iter >= S->maxiter || S->error) ? 1 : 0;
             }

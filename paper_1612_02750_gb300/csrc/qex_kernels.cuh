@@ -2,6 +2,8 @@
 // translation units of libqex_gpu share.
 #pragma once
 
+#include <cstdlib>
+
 #include "qex_common.cuh"
 
 namespace qex {
@@ -20,6 +22,8 @@ struct CgScalars {
     double delta2;    // reliable-update threshold factor delta^2 (0: only at convergence)
     double rmax2;     // max ||r||^2 since the last reliable update
     double true_rr;   // ||b - A x||^2 from the last FP64 recomputation
+    int max_cycle;    // > 0: a reliable update also follows max_cycle inner iterations without one
+    int ru_iter0;     // iteration count at the last reliable update
     int iters;        // completed iterations; its parity selects the current p buffer
     int maxiter;
     int done;         // true residual met tol
@@ -30,6 +34,23 @@ struct CgScalars {
     int trips;        // executions of the update kernel (graph loop guard)
     int x_nonzero;    // the initial guess has an element != 0 (or NaN); 0: the first residual is b
 };
+
+// Inner iterations after which a mixed-precision solve makes a reliable
+// update even when the iterated residual has not yet dropped by delta.  Over
+// a long cycle (thousands of iterations at small mass) the recursion residual
+// of the inner precision drifts away from b - A x, and the iteration keeps
+// reducing a residual that is no longer the true one; a bounded cycle resets
+// it to the FP64 true residual often enough.  16-bit links (step 2^-15) drift
+// faster than FP32 ones, hence the shorter cycle.  QEX_RU_CYCLE=<n> overrides
+// both, 0 turns the bound off.
+constexpr int kRuCycle16 = 100, kRuCycle32 = 500;
+inline int ru_max_cycle(qex_prec inner) {
+    if (inner == QEX_F64) return 0;
+    const char *e = getenv("QEX_RU_CYCLE");
+    if (!e || !*e) return (inner == QEX_F32_R12H || inner == QEX_F32_S16) ? kRuCycle16 : kRuCycle32;
+    const int v = atoi(e);
+    return v > 0 ? v : 0;
+}
 
 // Conditional-node handles of the CUDA-graph solve (active = 0 outside it).
 // The loop never runs more than maxiter + 4 trips (CgScalars::trips).
@@ -88,6 +109,8 @@ struct MrhsScalars {
     int nrhs;
     int iter;              // lockstep iteration count: its parity selects the p buffers
     int maxiter;
+    int max_cycle;         // > 0: a reliable update also follows max_cycle iterations without one
+    int ru_iter0;          // iter at the last reliable update
     int need_ru, halt, error;
     int reliable_updates;
     int nactive;
