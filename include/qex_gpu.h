@@ -101,7 +101,7 @@ typedef struct {
     int iters;               /* operator applications inside the CG iteration   */
     int reliable_updates;    /* FP64 true-residual recomputations (incl. final) */
     int converged;           /* 1 if the FP64 true residual met tol             */
-    int reserved;
+    int ff_updates;          /* of these, made in float-float arithmetic          */
     double true_rel_resid;   /* ||b - A x|| / ||b||, recomputed in FP64         */
     double time_ms;          /* wall time of the solve on the stream            */
 } qex_cg_stats;
@@ -308,6 +308,11 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  *   longer cycles (small mass) the inner recursion residual drifts away from
  *   the true one and the solve stalls.  The environment variable
  *   QEX_RU_CYCLE = n sets another bound (0: none), read at each solve.
+ *   The updates asked for before the iterated residual meets tol (and before
+ *   maxiter) run in float-float arithmetic (qex_true_residual, arith = 1) on
+ *   the FP32 pipes; the first one and the one that may end the solve run in
+ *   FP64, so convergence is always judged on an FP64 true residual.  The
+ *   environment variable QEX_RU_FF = 0 keeps every update in FP64.
  * b64, x64: F64 even half fields; x64 holds the initial guess on entry and the
  *   solution on return.  lng64/lng32 NULL = no Naik term.
  * Synchronises the stream before returning (fills stats, may be NULL).
@@ -349,6 +354,22 @@ qex_status qex_cg(const qex_lattice *lat, qex_prec inner, const void *fat64, con
 qex_status qex_cg_profile(const qex_lattice *lat, qex_prec inner, const void *fat64, const void *lng64,
                           const void *fat32, const void *lng32, double c_naik, double mass, const void *b64,
                           void *x64, int iters, void *stream, double *ms_out, int *n_out);
+
+/* ||b - A x|| / ||b|| with A = m^2 - D_eo D_oe on the even sites, from F64
+ * links (lng64 NULL = no Naik term) and F64 even half fields b64, x64, with
+ * the kernels of a reliable update: arith = 0 in FP64, arith = 1 in the
+ * float-float arithmetic of the intermediate updates (every real an
+ * unevaluated sum of two FP32 numbers, about 47 significant bits; link
+ * entries and b, x within 2^-100..2^100 of the root mean square of b's reals
+ * are carried at full precision, smaller ones as zero).  rel_resid (host)
+ * receives the result, 0 when b = 0.  Uses the lattice's work area and CG
+ * scalars (not while a solve on the same lattice runs).  Synchronises the
+ * stream.  Errors: as qex_dslash for the arguments, QEX_ERR_ARG (NULL
+ * rel_resid, arith not 0 or 1), QEX_ERR_NAN (NaN/Inf in the result).
+ * Paper: Sec. 4 (the solvers' stopping test, a relative true residual). */
+qex_status qex_true_residual(const qex_lattice *lat, const void *fat64, const void *lng64, double c_naik,
+                             double mass, const void *b64, const void *x64, int arith, double *rel_resid,
+                             void *stream);
 
 /* ---------------------------------------------------------------- force */
 

@@ -53,10 +53,10 @@ class CgItem(ctypes.Structure):
 
 class CgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
+                ("ff_updates", ctypes.c_int), ("true_rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def library_path() -> str:
@@ -107,6 +107,7 @@ def load():
         "qex_tune_info": (i, [vp, i, i, ip]),
         "qex_tune_set": (i, [vp, i, i, ip]),
         "qex_fma_rates": (i, [ctypes.POINTER(d), ctypes.POINTER(d), vp]),
+        "qex_true_residual": (i, [vp, vp, vp, d, d, vp, vp, i, ctypes.POINTER(d), vp]),
         "qex_launch_count": (ctypes.c_uint64, []),
         "qex_last_error": (ctypes.c_char_p, []),
         "qex_version": (ctypes.c_char_p, []),
@@ -127,7 +128,8 @@ def exported_symbols():
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
             "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch",
             "qex_cg_batch_tune_info", "qex_cg_batch_tune_set", "qex_long_links_prec", "qex_tune", "qex_tune_info",
-            "qex_tune_set", "qex_fma_rates", "qex_launch_count", "qex_last_error", "qex_version"]
+            "qex_tune_set", "qex_fma_rates", "qex_true_residual", "qex_launch_count", "qex_last_error",
+            "qex_version"]
 
 
 def _check(status: int):
@@ -384,6 +386,18 @@ def qex_cg_profile(lat: Lattice, inner, fat64, lng64, fat32, lng32, c_naik: floa
                                  float(c_naik), float(mass), _ptr(b64), _ptr(x64), int(iters), _stream(stream), ms,
                                  ctypes.byref(n)))
     return [ms[k] for k in range(n.value)]
+
+
+def qex_true_residual(lat: Lattice, fat64, lng64, c_naik: float, mass: float, b64, x64, arith: str = "f64",
+                      stream=None) -> float:
+    """||b - A x|| / ||b|| on the device, in FP64 (arith "f64") or in the
+    float-float arithmetic of the intermediate reliable updates ("ff")."""
+    if arith not in ("f64", "ff"):
+        raise ValueError("arith must be 'f64' or 'ff'")
+    out = ctypes.c_double()
+    _check(load().qex_true_residual(lat.handle, _ptr(fat64), _ptr(lng64), float(c_naik), float(mass), _ptr(b64),
+                                    _ptr(x64), 0 if arith == "f64" else 1, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 # -------------------------------------------------------------------- force

@@ -89,8 +89,17 @@ struct Solve {
     const double *b64;
     double *x64;
     bool defer_x;  // the FP32 iterate takes alpha p one iteration late, in kernel 1
+    bool ff_ok;    // intermediate reliable updates in float-float arithmetic (ru_ff.cu)
     CgBuffers B;
 };
+
+// Mixed solves run the reliable updates that cannot end the solve in
+// float-float arithmetic; QEX_RU_FF=0 keeps every update in FP64.
+static bool ru_ff_enabled(bool mixed) {
+    if (!mixed) return false;
+    const char *e = getenv("QEX_RU_FF");
+    return !(e && strcmp(e, "0") == 0);
+}
 
 #ifndef QEX_DEFER_X
 #define QEX_DEFER_X 1
@@ -190,7 +199,14 @@ static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStr
     a.epi = EPI_PLAIN;
     a.S = S;
     a.skip_zero_x = first ? 1 : 0;
+    // the FP64 kernels and their float-float twins (an update the iterated
+    // residual asks for before it meets tol): S->ru_ff lets one pair run
+    const bool ff = s.mixed && !first && s.ff_ok;
+    a.skip_ff = ff ? 1 : 0;
     if ((err = launch_dslash(lat, a, st))) return err;
+    if (ff && (err = launch_ru_ff(lat, 1, (const double *)s.fat64, (const double *)s.lng64, s.c3, s.m2,
+                                  (const double *)s.x64, nullptr, s.B.tmp64, nullptr, S, true, false, st)))
+        return err;
     a.out_parity = 0;
     a.in = s.B.tmp64;
     a.out = s.B.r64;
@@ -200,6 +216,10 @@ static qex_status enqueue_reliable_update(Solve &s, const GraphCtl &ctl, cudaStr
     a.m2 = s.m2;
     a.S = S;
     if ((err = launch_dslash(lat, a, st))) return err;
+    if (ff && (err = launch_ru_ff(lat, 2, (const double *)s.fat64, (const double *)s.lng64, s.c3, s.m2,
+                                  (const double *)s.x64, (const double *)s.b64, s.B.tmp64, s.B.r32, S, true, false,
+                                  st)))
+        return err;
     return launch_finish_ru(lat, s.B.r64, s.mixed ? s.B.r32 : nullptr, S, ctl, st);
 }
 
@@ -225,6 +245,7 @@ struct CgGraph {
     double c3, m2;
     const void *b64, *x64, *work;
     int pdl;  // kernels linked by programmatic dependencies
+    bool ff_ok;  // the updates carry float-float twins
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     unsigned long long kernels_per_trip, kernels_per_ru;
@@ -233,7 +254,7 @@ struct CgGraph {
 static bool same_key(const CgGraph *g, const Solve &s) {
     return g && g->inner == s.inner && g->fat64 == s.fat64 && g->lng64 == s.lng64 && g->fat32 == s.fat32 &&
            g->lng32 == s.lng32 && g->c3 == s.c3 && g->m2 == s.m2 && g->b64 == s.b64 && g->x64 == s.x64 &&
-           g->work == s.lat->work && g->pdl == s.lat->pdl;
+           g->work == s.lat->work && g->pdl == s.lat->pdl && g->ff_ok == s.ff_ok;
 }
 
 static void drop_graph(CgGraph *g) {
@@ -258,8 +279,9 @@ static qex_status build_graph(Solve &s, CgGraph **out) {
     G->x64 = s.x64;
     G->work = s.lat->work;
     G->pdl = s.lat->pdl;
+    G->ff_ok = s.ff_ok;
     G->kernels_per_trip = s.mixed ? 3 : 4;
-    G->kernels_per_ru = s.mixed ? 4 : 3;
+    G->kernels_per_ru = s.mixed ? (s.ff_ok ? 6 : 4) : 3;
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaSuccess;
     qex_status st = QEX_OK;
@@ -358,6 +380,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     Solve s;
     s.lat = lat;
     s.mixed = mixed;
+    s.ff_ok = ru_ff_enabled(mixed);
     s.inner = inner;
     s.fat64 = fat64;
     s.lng64 = lng64;
@@ -418,6 +441,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
     init.tol2 = tol * tol;
     init.delta2 = mixed ? delta * delta : 0.0;
     init.max_cycle = ru_max_cycle(inner);
+    init.ff_ok = s.ff_ok ? 1 : 0;
     init.maxiter = maxiter;
     CgScalars *h0 = lat->scalars_host, *h1 = lat->scalars_host2;
     QEX_CUDA(cudaStreamSynchronize(cst));  // the pinned slots are free
@@ -519,7 +543,7 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
         stats->iters = cur.iters;
         stats->reliable_updates = cur.reliable_updates > 0 ? cur.reliable_updates - 1 : 0;
         stats->converged = cur.done;
-        stats->reserved = 0;
+        stats->ff_updates = cur.ff_updates;
         stats->true_rel_resid = cur.bb > 0.0 ? sqrt(cur.true_rr / cur.bb) : 0.0;
         stats->time_ms = ms;
     }
@@ -553,6 +577,7 @@ extern "C" qex_status qex_cg_profile(const qex_lattice *latc, qex_prec inner, co
     Solve s;
     s.lat = lat;
     s.mixed = mixed;
+    s.ff_ok = ru_ff_enabled(mixed);
     s.inner = inner;
     s.fat64 = fat64;
     s.lng64 = lng64;
@@ -618,5 +643,72 @@ extern "C" qex_status qex_cg_profile(const qex_lattice *latc, qex_prec inner, co
     delete[] ev;
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "qex_cg_profile events");
+    return QEX_OK;
+}
+
+// ------------------------------------------------------ true residual
+
+// ||b - A x|| / ||b|| in FP64 or in the float-float arithmetic of the
+// intermediate reliable updates, with the update's own kernels.
+extern "C" qex_status qex_true_residual(const qex_lattice *latc, const void *fat64, const void *lng64, double c_naik,
+                                        double mass, const void *b64, const void *x64, int arith, double *rel_resid,
+                                        void *stream) {
+    qex_status st;
+    if ((st = check_lattice(latc))) return st;
+    if ((st = check_dslash_args(latc, QEX_F64, fat64, lng64, b64, x64))) return st;
+    if (!rel_resid || (arith != 0 && arith != 1)) {
+        set_error("need rel_resid and arith 0 (FP64) or 1 (float-float)");
+        return QEX_ERR_ARG;
+    }
+    qex_lattice *lat = const_cast<qex_lattice *>(latc);
+    if ((st = ensure_scratch(lat))) return st;
+    const size_t f64 = align256((size_t)lat->vh * 48);
+    if ((st = ensure_work(lat, 2 * f64))) return st;
+    char *w = (char *)lat->work;
+    void *tmp = w, *r = w + f64;
+    const cudaStream_t cst = as_stream(stream);
+    CgScalars init;
+    memset(&init, 0, sizeof(init));
+    QEX_CUDA(cudaStreamSynchronize(cst));  // the pinned slot is free
+    *lat->scalars_host = init;
+    QEX_CUDA(cudaMemcpyAsync(lat->scalars, lat->scalars_host, sizeof(CgScalars), cudaMemcpyHostToDevice, cst));
+    if ((st = launch_norm2(lat, QEX_F64, b64, nullptr, lat->scalars, cst))) return st;
+    if (arith == 0) {
+        DslashArgs a = {};
+        a.prec = QEX_F64;
+        a.fat = fat64;
+        a.lng = lng64;
+        a.c3 = c_naik;
+        a.out_parity = 1;
+        a.in = x64;
+        a.out = tmp;
+        a.epi = EPI_PLAIN;
+        a.S = lat->scalars;
+        if ((st = launch_dslash(lat, a, cst))) return st;
+        a.out_parity = 0;
+        a.in = tmp;
+        a.out = r;
+        a.epi = EPI_RESID;
+        a.q = x64;
+        a.b = (const double *)b64;
+        a.m2 = mass * mass;
+        if ((st = launch_dslash(lat, a, cst))) return st;
+    } else {
+        if ((st = launch_ru_ff(lat, 1, (const double *)fat64, (const double *)lng64, c_naik, mass * mass,
+                               (const double *)x64, nullptr, tmp, nullptr, lat->scalars, false, true, cst)))
+            return st;
+        if ((st = launch_ru_ff(lat, 2, (const double *)fat64, (const double *)lng64, c_naik, mass * mass,
+                               (const double *)x64, (const double *)b64, tmp, (float *)r, lat->scalars, false, true,
+                               cst)))
+            return st;
+    }
+    QEX_CUDA(cudaMemcpyAsync(lat->scalars_host, lat->scalars, sizeof(CgScalars), cudaMemcpyDeviceToHost, cst));
+    QEX_CUDA(cudaStreamSynchronize(cst));
+    const CgScalars &h = *lat->scalars_host;
+    if (!isfinite(h.bb) || !isfinite(h.true_rr)) {
+        set_error("NaN/Inf in the residual");
+        return QEX_ERR_NAN;
+    }
+    *rel_resid = h.bb > 0.0 ? sqrt(h.true_rr / h.bb) : 0.0;
     return QEX_OK;
 }

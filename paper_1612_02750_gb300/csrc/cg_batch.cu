@@ -1011,7 +1011,7 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
             stats[k].iters = h->iters[k];
             stats[k].reliable_updates = h->reliable_updates > 0 ? h->reliable_updates - 1 : 0;
             stats[k].converged = h->done[k];
-            stats[k].reserved = 0;
+            stats[k].ff_updates = 0;
             stats[k].true_rel_resid = h->bb[k] > 0.0 ? sqrt(h->true_rr[k] / h->bb[k]) : 0.0;
             stats[k].time_ms = ms;
         }

@@ -152,7 +152,8 @@ __device__ __forceinline__ double fused_total(const double *partials, int n, dou
 // that it holds no registers during the Dslash phases.
 struct FusedState {
     double rr, beta, rmax2, alpha, pAp;
-    int iters, trips, need_ru, error;
+    double rr_ru;
+    int iters, trips, need_ru, ru_ff, error;
 };
 
 template <typename R, int FMT, bool NAIK>
@@ -174,6 +175,7 @@ __device__ __forceinline__ void cg_fused_body(const FusedArgs<R> &A) {
         st.iters = S->iters;
         st.trips = S->trips;
         st.need_ru = 0;
+        st.ru_ff = 0;
         st.error = 0;
     }
     __syncthreads();
@@ -264,6 +266,8 @@ __device__ __forceinline__ void cg_fused_body(const FusedArgs<R> &A) {
                     const bool long_cycle = S->max_cycle > 0 && st.iters - S->ru_iter0 >= S->max_cycle;
                     if (rr_new <= S->stop2 || rr_new < S->delta2 * st.rmax2 || st.iters >= S->maxiter || long_cycle) {
                         st.need_ru = 1;  // rr keeps its value: beta then comes from the true residual
+                        st.ru_ff = (S->ff_ok && rr_new > S->stop2 && st.iters < S->maxiter) ? 1 : 0;
+                        st.rr_ru = rr_new;
                     } else {
                         st.beta = rr_new / st.rr;
                         st.rr = rr_new;
@@ -284,6 +288,10 @@ __device__ __forceinline__ void cg_fused_body(const FusedArgs<R> &A) {
         S->trips = st.trips;
         if (st.error) S->error = st.error;
         S->need_ru = st.need_ru;
+        if (st.need_ru) {
+            S->ru_ff = st.ru_ff;
+            S->rr_ru = st.rr_ru;
+        }
         S->halt = 1;
     }
 }

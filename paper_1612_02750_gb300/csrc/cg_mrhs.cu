@@ -391,7 +391,7 @@ extern "C" qex_status qex_cg_mrhs(const qex_lattice *latc, qex_prec inner, const
                 stats[q].iters = host->iters[q];
                 stats[q].reliable_updates = host->reliable_updates > 0 ? host->reliable_updates - 1 : 0;
                 stats[q].converged = host->done[q];
-                stats[q].reserved = 0;
+                stats[q].ff_updates = 0;
                 stats[q].true_rel_resid = host->bb[q] > 0.0 ? sqrt(host->true_rr[q] / host->bb[q]) : 0.0;
                 stats[q].time_ms = ms;
             }

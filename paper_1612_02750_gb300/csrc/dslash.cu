@@ -34,6 +34,7 @@ struct DsParams {
     int psel;
     int skip_zero_x;
     int reverse;        // walk the sites from the last index down
+    int skip_ff;
     double *partials;
     unsigned int *counter;
 };
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
     pdl_trigger();
     pdl_wait();  // everything below may read what earlier kernels wrote
     if (P.check_halt && P.S->halt) return;  // uniform over the grid
+    if (P.skip_ff && P.S->ru_ff) return;    // uniform: a float-float update
     // first residual from a zero initial guess: D x = 0 (uniform over the grid)
     const bool zero_x = P.skip_zero_x && !P.S->x_nonzero;
     if (EPI == EPI_PLAIN && zero_x) return;
@@ -172,20 +174,7 @@ __global__ void __launch_bounds__(kDslashBlock, DslashMinBlocks<R>::value) dslas
             }
         } else {
             // FP64 true residual: accept convergence, or continue with beta from it
-            S->true_rr = tot;
-            S->reliable_updates += 1;
-            if (!isfinite(tot)) {
-                S->error = 1;
-                S->halt = 1;
-                return;
-            }
-            S->ru_iter0 = S->iters;
-            S->beta = S->rr > 0.0 ? tot / S->rr : 0.0;
-            S->rr = tot;
-            S->rmax2 = tot;
-            S->need_ru = 0;
-            S->done = tot <= S->stop2 ? 1 : 0;
-            S->halt = (S->done || S->iters >= S->maxiter) ? 1 : 0;
+            take_true_residual(S, tot, true);
         }
     }
 }
@@ -242,6 +231,7 @@ static void launch_t(qex_lattice *lat, const DslashArgs &a, cudaStream_t st) {
     P.psel = a.psel;
     P.skip_zero_x = a.skip_zero_x;
     P.reverse = a.reverse;
+    P.skip_ff = a.skip_ff;
     P.partials = lat->partials;
     P.counter = lat->counter;
     int grid, block;

@@ -24,6 +24,11 @@ struct CgScalars {
     double true_rr;   // ||b - A x||^2 from the last FP64 recomputation
     int max_cycle;    // > 0: a reliable update also follows max_cycle inner iterations without one
     int ru_iter0;     // iteration count at the last reliable update
+    int ff_ok;        // intermediate reliable updates may run in float-float arithmetic (ru_ff.cu)
+    int ru_ff;        // the pending reliable update runs in float-float arithmetic
+    int ff_k;         // float-float updates carry the vectors times 2^ff_k (set with bb)
+    double rr_ru;     // iterated ||r||^2 when the pending reliable update was asked for
+    int ff_updates;   // reliable updates made in float-float arithmetic
     int iters;        // completed iterations; its parity selects the current p buffer
     int maxiter;
     int done;         // true residual met tol
@@ -34,6 +39,36 @@ struct CgScalars {
     int trips;        // executions of the update kernel (graph loop guard)
     int x_nonzero;    // the initial guess has an element != 0 (or NaN); 0: the first residual is b
 };
+
+// The CG scalars after a true residual ||b - A x||^2 = tot (last block of the
+// residual kernel, one thread).  `may_accept`: the residual was computed in
+// FP64 and may end the solve; a float-float one never does (the next update
+// that the iterated residual asks for at tol is an FP64 one).
+__device__ __forceinline__ void take_true_residual(CgScalars *S, double tot, bool may_accept) {
+    S->true_rr = tot;
+    S->reliable_updates += 1;
+    if (!may_accept) S->ff_updates += 1;
+    if (!isfinite(tot)) {
+        S->error = 1;
+        S->halt = 1;
+        return;
+    }
+    S->ru_iter0 = S->iters;
+    S->beta = S->rr > 0.0 ? tot / S->rr : 0.0;
+    S->rr = tot;
+    S->rmax2 = tot;
+    S->need_ru = 0;
+    S->done = (may_accept && tot <= S->stop2) ? 1 : 0;
+    S->halt = (S->done || S->iters >= S->maxiter) ? 1 : 0;
+}
+
+// Reliable updates in float-float arithmetic (ru_ff.cu): `stage` 1 writes
+// tmp = D_oe x64 (float pairs, 48 bytes a site), stage 2 r32 = b - m^2 x64 +
+// D_eo tmp rounded to FP32 and ||r||^2 (cg: the CG scalars as an update,
+// else only true_rr).  Unless `force`, both return at once when S->ru_ff is 0.
+qex_status launch_ru_ff(qex_lattice *lat, int stage, const double *fat64, const double *lng64, double c3,
+                        double m2, const double *x64, const double *b64, void *tmp, float *r32, CgScalars *S,
+                        bool cg, bool force, cudaStream_t st);
 
 // Inner iterations after which a mixed-precision solve makes a reliable
 // update even when the iterated residual has not yet dropped by delta.  Over
@@ -91,6 +126,8 @@ struct DslashArgs {
                          // iteration meets the links the first one read last while they are in L2)
     int skip_zero_x;     // EPI_PLAIN / EPI_RESID of the first residual: unless S->x_nonzero,
                          // PLAIN writes nothing and RESID takes D in = 0 (r = b)
+    int skip_ff;         // EPI_PLAIN / EPI_RESID of a mixed solve's update: return at once when
+                         // S->ru_ff (the float-float kernels run it)
 };
 
 qex_status launch_dslash(qex_lattice *lat, const DslashArgs &a, cudaStream_t st);
@@ -146,7 +183,7 @@ qex_status launch_update_p(qex_lattice *lat, qex_prec prec, const void *r, void 
                            cudaStream_t st);
 // x64 += (double) xh32 + alpha p with p = pbuf[iters & 1] (the update the
 // iteration left pending; pbuf NULL: none); xh32 = 0.
-qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, float *const pbuf[2], const CgScalars *S,
+qex_status launch_accum_x(qex_lattice *lat, double *x64, float *xh32, float *const pbuf[2], CgScalars *S,
                           cudaStream_t st);
 // r32 = (float) r64 (r32 may be NULL: only the graph condition is set),
 // alpha = 0 (no pending iterate update after a reliable update); loop
