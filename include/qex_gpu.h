@@ -308,11 +308,12 @@ qex_status qex_dot(const qex_lattice *lat, qex_prec prec, const void *a, const v
  *   longer cycles (small mass) the inner recursion residual drifts away from
  *   the true one and the solve stalls.  The environment variable
  *   QEX_RU_CYCLE = n sets another bound (0: none), read at each solve.
- *   The updates asked for before the iterated residual meets tol (and before
- *   maxiter) run in float-float arithmetic (qex_true_residual, arith = 1) on
- *   the FP32 pipes; the first one and the one that may end the solve run in
- *   FP64, so convergence is always judged on an FP64 true residual.  The
- *   environment variable QEX_RU_FF = 0 keeps every update in FP64.
+ *   The updates are FP64.  With the environment variable QEX_RU_FF = 1 (read
+ *   at each solve) those asked for before the iterated residual meets tol
+ *   (and before maxiter) run in float-float arithmetic (qex_true_residual,
+ *   arith = 1) on the FP32 pipes instead, as long as their error stays below
+ *   1e-3 of the residual; the first one and the one that may end the solve
+ *   stay FP64, so convergence is always judged on an FP64 true residual.
  * b64, x64: F64 even half fields; x64 holds the initial guess on entry and the
  *   solution on return.  lng64/lng32 NULL = no Naik term.
  * Synchronises the stream before returning (fills stats, may be NULL).

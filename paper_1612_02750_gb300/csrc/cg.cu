@@ -93,12 +93,13 @@ struct Solve {
     CgBuffers B;
 };
 
-// Mixed solves run the reliable updates that cannot end the solve in
-// float-float arithmetic; QEX_RU_FF=0 keeps every update in FP64.
+// Reliable updates are FP64 (the true-residual recomputation of the mixed
+// scheme); QEX_RU_FF=1 runs those that cannot end the solve in float-float
+// arithmetic instead (ru_ff.cu), the stopping test staying FP64.
 static bool ru_ff_enabled(bool mixed) {
     if (!mixed) return false;
     const char *e = getenv("QEX_RU_FF");
-    return !(e && strcmp(e, "0") == 0);
+    return e && strcmp(e, "1") == 0;
 }
 
 #ifndef QEX_DEFER_X

@@ -11,9 +11,10 @@ update and the one that may end the solve stay FP64.  These tests check
   are carried times 2^ff_k, a power of two taken from ||b||): b, x and
   2^+-90 b, 2^+-90 x give the same bits;
 * exact zeros (identity links, a zero x);
-* mixed solves with float-float updates against the same solves with FP64
-  updates (QEX_RU_FF=0): the same iteration counts up to rounding, FP64
-  stopping test, the oracle's true residual of the returned x;
+* mixed solves with float-float updates (QEX_RU_FF=1; FP64 updates are the
+  default) against the same solves with FP64 updates: the same iteration
+  counts up to rounding, FP64 stopping test, the oracle's true residual of
+  the returned x;
 * that the updates give way to FP64 once their error (about 1e-13 of
   ||x|| + ||b||) would reach 1e-3 of the residual: at small mass on Haar
   links ||x|| is about 1400 ||b||, and with an update every 50 iterations
@@ -151,9 +152,9 @@ def test_solves_with_float_float_updates(q, oracle_mod, monkeypatch, mode, naik)
     lng_i = q.qex_convert_links(lat, "f64", lng64, q.qex_long_links_prec(inner)) if naik else None
     b64 = q.qex_pack_field(lat, "f64", 0, dev(b))
     monkeypatch.setenv("QEX_CG_MODE", mode)
-    monkeypatch.setenv("QEX_RU_FF", "0")
+    monkeypatch.delenv("QEX_RU_FF", raising=False)  # default: FP64 updates
     st0, s0, x0 = _solve(q, lat, fat64, lng64, fat_i, lng_i, c3, mass, b64, inner)
-    monkeypatch.delenv("QEX_RU_FF")
+    monkeypatch.setenv("QEX_RU_FF", "1")
     st1, s1, x1 = _solve(q, lat, fat64, lng64, fat_i, lng_i, c3, mass, b64, inner)
     assert st0 == st1 == 0 and s0["converged"] and s1["converged"]
     assert s0["ff_updates"] == 0 and 1 <= s1["ff_updates"] < s1["reliable_updates"], (s0, s1)
@@ -168,11 +169,12 @@ def test_graph_and_host_agree_bitwise_with_float_float_updates(q, monkeypatch):
     lat, u, w, b, _, fat64, lng64 = _setup(q, dims, False, 23)
     fat_i = q.qex_convert_links(lat, "f64", fat64, inner)
     b64 = q.qex_pack_field(lat, "f64", 0, dev(b))
+    monkeypatch.setenv("QEX_RU_FF", "1")
     monkeypatch.setenv("QEX_CG_MODE", "graph")
     st_g, s_g, x_g = _solve(q, lat, fat64, None, fat_i, None, 0.0, mass, b64, inner, delta=0.05)
     monkeypatch.setenv("QEX_CG_MODE", "host")
     st_h, s_h, x_h = _solve(q, lat, fat64, None, fat_i, None, 0.0, mass, b64, inner, delta=0.05)
-    assert st_g == st_h == 0 and s_g["reliable_updates"] >= 3
+    assert st_g == st_h == 0 and s_g["reliable_updates"] >= 3 and s_g["ff_updates"] >= 1
     assert (s_g["iters"], s_g["reliable_updates"]) == (s_h["iters"], s_h["reliable_updates"])
     assert np.array_equal(x_g, x_h)
 
@@ -185,6 +187,7 @@ def test_float_float_updates_give_way_at_small_mass(q, oracle_mod, monkeypatch):
     fat_i = q.qex_convert_links(lat, "f64", fat64, inner)
     b64 = q.qex_pack_field(lat, "f64", 0, dev(b))
     monkeypatch.setenv("QEX_RU_CYCLE", "50")
+    monkeypatch.setenv("QEX_RU_FF", "1")
     st, s, x = _solve(q, lat, fat64, None, fat_i, None, 0.0, mass, b64, inner)
     assert st == 0 and s["converged"], s
     assert 1 <= s["ff_updates"] < s["reliable_updates"] - 10, s
