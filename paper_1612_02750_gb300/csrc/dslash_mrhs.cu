@@ -19,13 +19,32 @@ namespace qex {
 // b / ngroups and group b % ngroups, so the blocks that reuse a link run back
 // to back and find it in L2.
 constexpr int kMrhsBlock = 256;  // threads (sites) per block
-// Resident blocks per SM (the register cap: 128 per thread leaves the KR
-// accumulators, the KR input vectors of a hop and a decoded link in registers;
-// the KR independent mat-vecs supply the instruction-level parallelism that
-// the lower occupancy gives up).
-constexpr int kMrhsMinBlocks = 2;
-template <typename R> struct MrhsPerThread { static constexpr int value = 4; };
-template <> struct MrhsPerThread<double> { static constexpr int value = 2; };
+// Right-hand sides per thread (KR) and resident blocks per SM (MINB, the
+// register cap) by precision and epilogue.  The plain Dslash keeps KR = 4 at 2
+// blocks (128 registers: the four accumulators, the four input vectors of a
+// hop and a decoded link; the four independent mat-vecs supply the
+// instruction-level parallelism that the lower occupancy gives up).  The CG
+// epilogues, which also gather the directions or read the q vectors, run
+// faster at KR = 2 and 4 blocks (24^4, 16 sources: the batched mixed CG
+// 0.42 s against 0.46 s); FP64 keeps KR = 2 at 2 blocks (it spills above).
+#ifndef QEX_MRHS_KR_CG
+#define QEX_MRHS_KR_CG 2
+#endif
+#ifndef QEX_MRHS_MIN_BLOCKS_CG
+#define QEX_MRHS_MIN_BLOCKS_CG 4
+#endif
+template <typename R, int EPI>
+struct MrhsShape {
+    static constexpr int kr = EPI == EPI_PLAIN ? 4 : QEX_MRHS_KR_CG;
+    static constexpr int minb = EPI == EPI_PLAIN ? 2 : QEX_MRHS_MIN_BLOCKS_CG;
+};
+template <int EPI>
+struct MrhsShape<double, EPI> {
+    static constexpr int kr = 2;
+    static constexpr int minb = 2;
+};
+// the largest persistent grid times KR of any reducing variant (partials per launch)
+constexpr int kMrhsMaxPartialsPerSm = 8;
 
 template <typename R>
 struct MParams {
@@ -47,8 +66,8 @@ struct MParams {
 };
 
 template <typename R, int FMT, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kMrhsBlock, kMrhsMinBlocks) dslash_mrhs_kernel(const MParams<R> P) {
-    constexpr int KR = MrhsPerThread<R>::value;
+__global__ void __launch_bounds__(kMrhsBlock, (MrhsShape<R, EPI>::minb)) dslash_mrhs_kernel(const MParams<R> P) {
+    constexpr int KR = MrhsShape<R, EPI>::kr;
     __shared__ double wsum[kMrhsBlock / 32][KR];
     __shared__ unsigned int is_last;
     MrhsScalars *S = P.S;
@@ -226,7 +245,7 @@ static void launch_m(const qex_lattice *lat, const MrhsArgs &a, cudaStream_t st)
     P.c3 = (R)a.c3;
     P.p = a.out_parity;
     P.nrhs = a.nrhs;
-    constexpr int KR = MrhsPerThread<R>::value;
+    constexpr int KR = MrhsShape<R, EPI>::kr;
     P.ngroups = (a.nrhs + KR - 1) / KR;
     P.in = (const R *)a.in;
     P.out = (R *)a.out;
@@ -244,7 +263,7 @@ static void launch_m(const qex_lattice *lat, const MrhsArgs &a, cudaStream_t st)
     const int total = nsb * P.ngroups;
     int gx = total;
     if (EPI == EPI_NORMAL || EPI == EPI_RESID) {  // persistent grid, a multiple of ngroups
-        int cap = sm_count() * kMrhsMinBlocks;
+        int cap = sm_count() * MrhsShape<R, EPI>::minb;
         cap -= cap % P.ngroups;
         if (cap < P.ngroups) cap = P.ngroups;
         gx = total < cap ? total : cap;
@@ -268,7 +287,7 @@ qex_status launch_dslash_mrhs(qex_lattice *lat, const MrhsArgs &a, cudaStream_t 
     if (a.epi == EPI_NORMAL || a.epi == EPI_RESID) {
         qex_status s = ensure_scratch(lat);
         if (s) return s;
-        const size_t need = (size_t)(sm_count() * kMrhsMinBlocks + 1) * MrhsPerThread<float>::value;
+        const size_t need = (size_t)(sm_count() + 1) * kMrhsMaxPartialsPerSm;
         if ((size_t)lat->partials_len < need) {
             set_error("internal: partials buffer too small for %d right-hand sides", a.nrhs);
             return QEX_ERR_ARG;
