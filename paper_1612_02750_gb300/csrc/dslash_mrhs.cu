@@ -13,8 +13,9 @@
 namespace qex {
 
 // Thread mapping: one output site per thread and a group of KR right-hand
-// sides per thread (KR = 4 in FP32, 2 in FP64, held in registers): each
-// link is loaded and decoded once per group and applied to all KR vectors.
+// sides per thread (held in registers; KR by precision and epilogue, see
+// MrhsShape): each link is loaded and decoded once per group and applied to
+// all KR vectors.
 // A block is 256 sites of one group; linear block b covers site block
 // b / ngroups and group b % ngroups, so the blocks that reuse a link run back
 // to back and find it in L2.
