@@ -56,12 +56,13 @@ def _problem(q, dims, mass, seed, naik, inner, zero=False):
 SPECS = [((4, 4, 4, 4), 0.1), ((6, 4, 4, 10), 0.05), ((8, 8, 4, 8), 0.2), ((8, 4, 6, 8), 0.08), ((4, 6, 4, 4), 0.3)]
 
 
-@pytest.mark.parametrize("inner", ["f64", "f32r12h"])
+@pytest.mark.parametrize("inner", ["f64", "f32", "f32r12", "f32r12h", "f32s16"])
 @pytest.mark.parametrize("naik", [False, True])
 def test_batch_matches_oracle_and_single(q, oracle_mod, inner, naik):
     """Five lattices of different extents and masses (one with a zero source)
-    solved in one batch: each meets an oracle-recomputed true residual of
-    1.05e-10 and agrees with the oracle's solve to 1e-13."""
+    solved in one batch, in every inner format: each meets an
+    oracle-recomputed true residual of 1.05e-10 and agrees with the oracle's
+    1e-13 solve to 1e-7."""
     probs = [_problem(q, d, m, 70 + k, naik, inner, zero=(k == 3)) for k, (d, m) in enumerate(SPECS)]
     st, stats = q.qex_cg_batch([p[0] for p in probs], inner, tol=1e-10, delta=0.1)
     assert st == 0 and all(s["converged"] for s in stats), stats

@@ -122,12 +122,13 @@ def torch_cat(q, parts):
     return torch.cat(parts).contiguous()
 
 
-@pytest.mark.parametrize("inner", ["f64", "f32r12"])
+@pytest.mark.parametrize("inner", ["f64", "f32", "f32r12", "f32r12h", "f32s16"])
 @pytest.mark.parametrize("naik", [False, True])
 def test_cg_mrhs(q, oracle_mod, inner, naik):
-    """Five sources (one of them zero) solved together: every solution has an
-    oracle-recomputed true residual <= 1.05e-10 and agrees with the oracle's
-    solve of the same source to 1e-13."""
+    """Five sources (one of them zero, the others 1e-2 .. 1e2 in size) solved
+    together, in every inner format (long links in qex_long_links_prec):
+    every solution has an oracle-recomputed true residual <= 1.05e-10 and
+    agrees with the oracle's 1e-13 solve of the same source to 1e-7."""
     import torch
 
     dims = (8, 8, 4, 8)
@@ -146,7 +147,7 @@ def test_cg_mrhs(q, oracle_mod, inner, naik):
     fat64 = q.qex_pack_links(lat, "f64", dev(u))
     lng64 = q.qex_pack_links(lat, "f64", dev(w)) if naik else None
     fat32 = q.qex_convert_links(lat, "f64", fat64, inner) if inner != "f64" else None
-    lng32 = q.qex_convert_links(lat, "f64", lng64, "f32") if (naik and inner != "f64") else None
+    lng32 = q.qex_convert_links(lat, "f64", lng64, q.qex_long_links_prec(inner)) if (naik and inner != "f64") else None
     B = torch_cat(q, [q.qex_pack_field(lat, "f64", 0, dev(b)) for b in srcs])
     X = torch.zeros_like(B)
     st, stats = q.qex_cg_mrhs(lat, inner, fat64, lng64, fat32, lng32, c3, m, 5, B, X, tol=1e-10, delta=0.1)
