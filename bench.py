@@ -339,8 +339,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
 
     def step(inner=INNER):
-        q.qex_pack_links(lat, "f64", U_d, fat64)
-        q.qex_convert_links(lat, "f64", fat64, INNER, fat32)
+        q.qex_pack_links_pair(lat, U_d, INNER, fat64, fat32)  # FP64 and 16-bit two-row sets, one pass
         q.qex_pack_field(lat, "f64", 0, B_d, bh)
         x.zero_()
         _, stats = q.qex_cg(lat, inner, fat64, None, fat32, None, 0.0, mass, bh, x, tol=TOL, maxiter=200000,

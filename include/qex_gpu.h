@@ -173,6 +173,17 @@ int qex_long_links_prec(qex_prec prec);
 qex_status qex_pack_links(const qex_lattice *lat, qex_prec prec, const double *lex_links,
                           void *internal, void *stream);
 
+/* Canonical lex links -> the internal F64 set (internal64) and a second set of
+ * an FP32 precision (internal2, e.g. the inner links of a mixed solve: the
+ * inner format for fat links, qex_long_links_prec(inner) for long links) in
+ * one pass over lex_links; bit for bit what qex_pack_links to F64 followed by
+ * qex_convert_links from F64 gives.  No buffer may overlap another.
+ * Errors: QEX_ERR_ARG (NULL, second = QEX_F64 or unknown), QEX_ERR_ALIGN.
+ * Paper: no counterpart (layout conversion).
+ */
+qex_status qex_pack_links_pair(const qex_lattice *lat, const double *lex_links, void *internal64,
+                               qex_prec second, void *internal2, void *stream);
+
 /* Internal links -> canonical lex links (complex double).
  * Paper: no counterpart (layout conversion).
  */

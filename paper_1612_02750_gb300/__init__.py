@@ -84,6 +84,7 @@ def load():
         "qex_links_bytes": (sz, [vp, i]),
         "qex_field_bytes": (sz, [vp, i]),
         "qex_pack_links": (i, [vp, i, vp, vp, vp]),
+        "qex_pack_links_pair": (i, [vp, vp, vp, i, vp, vp]),
         "qex_unpack_links": (i, [vp, i, vp, vp, vp]),
         "qex_pack_field": (i, [vp, i, i, vp, vp, vp]),
         "qex_unpack_field": (i, [vp, i, i, vp, vp, vp]),
@@ -124,7 +125,7 @@ def exported_symbols():
     """Names of the C entry points this binding wraps."""
     return ["qex_lattice_create", "qex_lattice_destroy", "qex_volume", "qex_half_volume", "qex_eo_index",
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
-            "qex_pack_links", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
+            "qex_pack_links", "qex_pack_links_pair", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
             "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
             "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch",
             "qex_cg_batch_tune_info", "qex_cg_batch_tune_set", "qex_long_links_prec", "qex_tune", "qex_tune_info",
@@ -262,6 +263,18 @@ def qex_pack_links(lat: Lattice, prec, lex_links, out=None, stream=None):
     out = empty_links(lat, prec) if out is None else out
     _check(load().qex_pack_links(lat.handle, _prec(prec), _ptr(lex_links), _ptr(out), _stream(stream)))
     return out
+
+
+def qex_pack_links_pair(lat: Lattice, lex_links, second, out64=None, out2=None, stream=None):
+    """Canonical links -> (internal F64 set, internal set of precision
+    ``second``) in one pass; returns both."""
+    if lex_links.dtype != torch.complex128:
+        raise TypeError("canonical links must be complex128")
+    out64 = empty_links(lat, "f64") if out64 is None else out64
+    out2 = empty_links(lat, second) if out2 is None else out2
+    _check(load().qex_pack_links_pair(lat.handle, _ptr(lex_links), _ptr(out64), _prec(second), _ptr(out2),
+                                      _stream(stream)))
+    return out64, out2
 
 
 def qex_unpack_links(lat: Lattice, prec, internal, out=None, stream=None):

@@ -433,6 +433,20 @@ qex_status qex_unpack_field(const qex_lattice *lat, qex_prec prec, int parity, c
     return QEX_OK;
 }
 
+qex_status qex_pack_links_pair(const qex_lattice *lat, const double *lex_links, void *internal64, qex_prec second,
+                               void *internal2, void *stream) {
+    qex_status st;
+    if ((st = check_lattice(lat)) || (st = check_prec(second)) || (st = check_ptrs(lex_links, internal64)) ||
+        (st = check_ptrs(internal2, internal64)))
+        return st;
+    if (second == QEX_F64) {
+        set_error("the second link set of qex_pack_links_pair must be an FP32 format");
+        return QEX_ERR_ARG;
+    }
+    return launch_pack_links_range(const_cast<qex_lattice *>(lat), lex_links, internal64, second, internal2, 0,
+                                   (int)lat->vh, as_stream(stream));
+}
+
 qex_status qex_convert_links(const qex_lattice *lat, qex_prec from, const void *in, qex_prec to, void *out,
                              void *stream) {
     qex_status st;

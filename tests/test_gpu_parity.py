@@ -115,6 +115,31 @@ def test_pack_roundtrip_bit_exact(q, dims):
     assert np.array_equal(host(q.qex_unpack_links(lat, "f64", l64)), u.astype(np.complex64).astype(np.complex128))
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 10), (10, 6, 4, 8)])
+def test_pack_links_pair_equals_pack_then_convert(q, dims):
+    """One pass from canonical links to the FP64 set and an FP32-class set
+    gives the same bits as qex_pack_links to F64 followed by
+    qex_convert_links, in every FP32 format (non-unitary Gaussian links for
+    the scaled 16-bit one); an F64 second set and NULL buffers are refused."""
+    import torch
+
+    s = fg.rng_streams(5)
+    lat = q.Lattice(dims)
+    for second, kind in (("f32", "haar"), ("f32r12", "haar"), ("f32r12h", "haar"), ("f32s16", "gauss3")):
+        u = fg.random_links(dims, kind, s["links"])
+        ref64 = q.qex_pack_links(lat, "f64", dev(u))
+        ref2 = q.qex_convert_links(lat, "f64", ref64, second)
+        got64 = q.empty_links(lat, "f64").fill_(float("nan"))
+        got2 = q.empty_links(lat, second).fill_(float("nan"))
+        q.qex_pack_links_pair(lat, dev(u), second, got64, got2)
+        # compared as bits: 16-bit words read as floats can be NaN patterns
+        assert torch.equal(got64.view(torch.int64), ref64.view(torch.int64)), second
+        assert torch.equal(got2.view(torch.int32), ref2.view(torch.int32)), second
+    lib = q.load()
+    assert lib.qex_pack_links_pair(lat.handle, dev(u).data_ptr(), got64.data_ptr(), 0, got2.data_ptr(), None) == 1
+    assert lib.qex_pack_links_pair(lat.handle, None, got64.data_ptr(), 3, got2.data_ptr(), None) == 1
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 10)])
 def test_convert_field_bit_exact(q, dims):
     """Half fields: F64 -> F32 rounds each real to nearest (numpy's cast),
