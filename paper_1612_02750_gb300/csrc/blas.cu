@@ -64,7 +64,13 @@ update_xr_kernel(int vh, R *__restrict__ x, R *__restrict__ r, R *pbuf0, R *pbuf
     pdl_trigger();
     pdl_wait();
     if (S->halt) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_conditions(ctl, 0u, 0u);
+        // an earlier iteration of the same graph trip asked for a reliable
+        // update (keep its conditions) or stopped on an error (end the loop)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned int ru = (S->need_ru && !S->error) ? 1u : 0u;
+            set_conditions(ctl, ru, ru);
+            S->idle_iters += 1;
+        }
         return;
     }
     // fail-safe: stop unless the last block (which runs after this block's

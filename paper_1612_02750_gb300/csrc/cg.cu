@@ -13,10 +13,10 @@
 // then moves r and A p only); a reliable update takes the pending alpha p
 // itself and zeroes alpha.
 // alpha, beta and the norms stay in device memory.  By default the whole
-// solve runs as one CUDA graph: a conditional WHILE node around the three
-// kernels, followed inside the loop by a conditional IF node holding the
-// reliable update (FP64 true residual); kernel 3 and the update's last
-// kernel set the two conditions.  The loop ends when the true residual meets
+// solve runs as one CUDA graph: a conditional WHILE node around
+// QEX_GRAPH_UNROLL iterations of the three kernels, followed inside the loop
+// by a conditional IF node holding the reliable update (FP64 true residual);
+// kernel 3 and the update's last kernel set the two conditions.  The loop ends when the true residual meets
 // tol, on the iteration cap, or on a NaN, and in any case after maxiter + 4
 // trips.  Setting QEX_CG_MODE=host instead enqueues batches of iterations
 // from the host and runs the reliable updates between batches.  A mixed
@@ -104,6 +104,14 @@ static bool ru_ff_enabled(bool mixed) {
 
 #ifndef QEX_DEFER_X
 #define QEX_DEFER_X 1
+#endif
+// CG iterations per trip of the graph's WHILE node.  Evaluating the loop and
+// IF conditions costs a few microseconds a trip; the iterations after one
+// that asks for a reliable update in the same trip find the solve halted and
+// return at once.  32^4 solve: 20.87-20.91 ms (1), 20.44 (2), 19.82-19.83
+// (4), 19.74-19.75 (8), the last two on a faster box.
+#ifndef QEX_GRAPH_UNROLL
+#define QEX_GRAPH_UNROLL 8
 #endif
 #ifndef QEX_REVERSE_SECOND
 #define QEX_REVERSE_SECOND 1
@@ -249,7 +257,7 @@ struct CgGraph {
     bool ff_ok;  // the updates carry float-float twins
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    unsigned long long kernels_per_trip, kernels_per_ru;
+    unsigned long long kernels_per_iter, kernels_per_ru;
 };
 
 static bool same_key(const CgGraph *g, const Solve &s) {
@@ -281,7 +289,7 @@ static qex_status build_graph(Solve &s, CgGraph **out) {
     G->work = s.lat->work;
     G->pdl = s.lat->pdl;
     G->ff_ok = s.ff_ok;
-    G->kernels_per_trip = s.mixed ? 3 : 4;
+    G->kernels_per_iter = s.mixed ? 3 : 4;
     G->kernels_per_ru = s.mixed ? (s.ff_ok ? 6 : 4) : 3;
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaSuccess;
@@ -304,7 +312,7 @@ static qex_status build_graph(Solve &s, CgGraph **out) {
         if ((e = cudaGraphConditionalHandleCreate(&ctl.ru, body, 0, 0))) break;
         // loop body: the three iteration kernels, then IF (reliable update)
         if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
-        st = enqueue_iteration(s, ctl, cs);
+        for (int u = 0; u < QEX_GRAPH_UNROLL && !st; ++u) st = enqueue_iteration(s, ctl, cs);
         cudaStreamCaptureStatus cst;
         const cudaGraphNode_t *deps = nullptr;
         size_t ndeps = 0;
@@ -473,7 +481,8 @@ extern "C" qex_status qex_cg(const qex_lattice *latc, qex_prec inner, const void
         if ((st = fetch_scalars(lat, 0, cst)) || (st = wait_scalars(lat, 0))) return st;
         cur = *h0;
         const unsigned long long rus = cur.reliable_updates > 1 ? cur.reliable_updates - 1 : 0;
-        note_launches(G->kernels_per_trip * (unsigned long long)cur.trips + G->kernels_per_ru * rus);
+        note_launches(G->kernels_per_iter * (unsigned long long)(cur.trips + cur.idle_iters) +
+                      G->kernels_per_ru * rus);
     } else if (!cur.done && !cur.halt && use_fused) {
         // persistent inner iterations, FP64 reliable updates in between
         while (!cur.done && !cur.error) {

@@ -29,6 +29,7 @@ struct CgScalars {
     int ff_k;         // float-float updates carry the vectors times 2^ff_k (set with bb)
     double rr_ru;     // iterated ||r||^2 when the pending reliable update was asked for
     int ff_updates;   // reliable updates made in float-float arithmetic
+    int idle_iters;   // iterations whose kernels found the solve halted (queued or graph-unrolled)
     int iters;        // completed iterations; its parity selects the current p buffer
     int maxiter;
     int done;         // true residual met tol
