@@ -105,14 +105,6 @@ static bool ru_ff_enabled(bool mixed) {
 #ifndef QEX_DEFER_X
 #define QEX_DEFER_X 1
 #endif
-// CG iterations per trip of the graph's WHILE node.  Evaluating the loop and
-// IF conditions costs a few microseconds a trip; the iterations after one
-// that asks for a reliable update in the same trip find the solve halted and
-// return at once.  32^4 solve: 20.87-20.91 ms (1), 20.44 (2), 19.82-19.83
-// (4), 19.74-19.75 (8), the last two on a faster box.
-#ifndef QEX_GRAPH_UNROLL
-#define QEX_GRAPH_UNROLL 8
-#endif
 #ifndef QEX_REVERSE_SECOND
 #define QEX_REVERSE_SECOND 1
 #endif

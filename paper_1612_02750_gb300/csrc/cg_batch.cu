@@ -62,6 +62,7 @@ struct BatchScalars {
     int max_cycle;            // > 0: a reliable update also follows max_cycle iterations without one
     double tol2, delta2;
     int n, iter, maxiter, halt, error, any_need, nactive, reliable_updates, trips;
+    int idle_iters;  // iterations whose update kernel found the batch halted
 };
 
 enum BatchRole {
@@ -237,7 +238,13 @@ batch_update_kernel(const LatDesc *__restrict__ descs, BatchScalars *S, double *
     __shared__ double smem[32];
     __shared__ double tot[kMaxRhs];
     if (S->halt) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_conds(ctl, 0u, 0u);
+        // an earlier iteration of the same graph trip asked for a reliable
+        // update (keep its conditions) or the batch stopped (end the loop)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned int ru = (S->any_need && !S->error) ? 1u : 0u;
+            set_conds(ctl, ru, ru);
+            S->idle_iters += 1;
+        }
         return;
     }
     // fail-safe: stop unless the last block sets the conditions again
@@ -645,7 +652,7 @@ static qex_status build_batch_graph(BatchCtx *c, const BatchLaunch &b) {
         cudaGraph_t body = wp.conditional.phGraph_out[0];
         if ((e = cudaGraphConditionalHandleCreate(&ctl.ru, body, 0, 0))) break;
         if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
-        st = enqueue_iteration(b, ctl, cs);
+        for (int u = 0; u < QEX_GRAPH_UNROLL && !st; ++u) st = enqueue_iteration(b, ctl, cs);
         cudaStreamCaptureStatus cst;
         const cudaGraphNode_t *deps = nullptr;
         size_t ndeps = 0;
@@ -977,7 +984,7 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
         if (use_graph) {
             QEX_CUDA(cudaGraphLaunch(c->exec, s));
             if ((st = fetch())) return st;
-            note_launches(3ull * (unsigned long long)h->trips +
+            note_launches(3ull * (unsigned long long)(h->trips + h->idle_iters) +
                           (mixed ? 6ull : 4ull) * (unsigned long long)(h->reliable_updates > 1 ? h->reliable_updates - 1 : 0));
         } else {
             const int batch = 8;

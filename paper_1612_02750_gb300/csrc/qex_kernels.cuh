@@ -71,6 +71,15 @@ qex_status launch_ru_ff(qex_lattice *lat, int stage, const double *fat64, const 
                         double m2, const double *x64, const double *b64, void *tmp, float *r32, CgScalars *S,
                         bool cg, bool force, cudaStream_t st);
 
+// CG iterations per trip of a CUDA-graph solve's WHILE node (single lattice and batched).  Evaluating the loop and
+// IF conditions costs a few microseconds a trip; the iterations after one
+// that asks for a reliable update in the same trip find the solve halted and
+// return at once.  32^4 solve: 20.87-20.91 ms (1), 20.44 (2), 19.82-19.83
+// (4), 19.74-19.75 (8), the last two on a faster box.
+#ifndef QEX_GRAPH_UNROLL
+#define QEX_GRAPH_UNROLL 8
+#endif
+
 // Inner iterations after which a mixed-precision solve makes a reliable
 // update even when the iterated residual has not yet dropped by delta.  Over
 // a long cycle (thousands of iterations at small mass) the recursion residual
