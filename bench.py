@@ -380,11 +380,13 @@ def run_native(args):
         torch.cuda.synchronize()
         clocks_e2e = Clocks(torch.cuda.current_device())
         clocks_e2e.start()
-        solve_ms = []
+        solve_ms, call_ms = [], []
         t0 = time.perf_counter()
         for _ in range(args.steps):
+            c0 = time.perf_counter()
             _, _, st_h = q.qex_cg_host(lat, INNER, U_h, None, 0.0, mass, B_h, X_h, tol=TOL, maxiter=200000,
                                        delta=DELTA)
+            call_ms.append((time.perf_counter() - c0) * 1e3)
             solve_ms.append(st_h["time_ms"])
         torch.cuda.synchronize()
         e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
@@ -406,6 +408,7 @@ def run_native(args):
                "h2d_plain_copy_ms": round(min(link), 3),
                "h2d_plain_copy_gbs": round(h2d_bytes / (min(link) * 1e-3) / 1e9, 1),
                "solve_ms_median": round(statistics.median(solve_ms), 3),
+               "call_ms_median": round(statistics.median(call_ms), 3), "call_ms_max": round(max(call_ms), 3),
                "clocks_sm_mhz": clk_e2e.get("sm_mhz"), "clock_reasons": clk_e2e.get("reasons")}
 
     # the same step with the optional float-float intermediate reliable updates (QEX_RU_FF=1), reported
