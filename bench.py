@@ -153,6 +153,14 @@ class Clocks:
                  "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the sampler's start-up (driver and NVML initialisation) must not overlap the timed region: a
+        # host-path solve that ran alongside it took 72-118 ms instead of 23; wait for its first sample
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.file.name) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self) -> dict:
         if not self.proc:
