@@ -153,6 +153,9 @@ class Clocks:
                  "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            if self.file is not None:
+                self.file.close()
+                os.unlink(self.file.name)
             return
         # the sampler's start-up (driver and NVML initialisation) must not overlap the timed region: a
         # host-path solve that ran alongside it took 72-118 ms instead of 23; wait for its first sample

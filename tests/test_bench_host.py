@@ -79,6 +79,47 @@ def test_clock_parsing(tmp_path):
     assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
 
 
+def test_clock_sampler_waits_for_its_first_sample(tmp_path, monkeypatch):
+    """Clocks.start() returns only once the sampler has written a sample (its
+    start-up must not overlap a timed region), and at most after about 3 s
+    when none comes; stop() parses what it wrote.  A fake nvidia-smi on PATH
+    stands in for the real one: it sleeps 0.4 s, then writes a sample every
+    0.1 s."""
+    sys.path.insert(0, ROOT)
+    import time
+
+    import bench
+
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nsleep 0.4\nwhile true; do\n"
+                    "  echo '2070, 2070, 900.0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "  sleep 0.1\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    c = bench.Clocks(0)
+    t0 = time.time()
+    c.start()
+    waited = time.time() - t0
+    assert os.path.getsize(c.file.name) > 0 and 0.3 < waited < 3.5, waited
+    time.sleep(0.3)
+    out = c.stop()
+    assert out["sm_mhz"] == 2070 and out["reasons"] == [] and out["samples"] >= 2
+
+    # a sampler that never writes: start() gives up after about 3 s
+    fake.write_text("#!/bin/sh\nsleep 30\n")
+    c = bench.Clocks(0)
+    t0 = time.time()
+    c.start()
+    assert 2.5 < time.time() - t0 < 5.0
+    assert c.stop()["samples"] == 0
+
+    # no nvidia-smi at all
+    monkeypatch.setenv("PATH", str(tmp_path / "none"))
+    c = bench.Clocks(0)
+    c.start()
+    assert c.proc is None and c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
 def test_traffic_guard_uses_source_hash():
     sys.path.insert(0, ROOT)
     import bench
