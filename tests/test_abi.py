@@ -141,6 +141,19 @@ def test_argument_errors(lib):
     assert lib.qex_links_bytes(h, 4) == 4 * 128 * 40  # 18 16-bit reals + an FP32 step per link
     assert lib.qex_field_bytes(h, 4) == 64 * 6 * 4
     assert lib.qex_pack_links(h, 5, None, None, None) == 1  # unknown precision
+    # one-pass pack: NULL buffers, an F64 or unknown second format (all refused before any launch)
+    bufs = [np.zeros(64, dtype=np.float64) for _ in range(3)]
+    ptrs = [b.ctypes.data for b in bufs]
+    assert lib.qex_pack_links_pair(h, None, ptrs[1], 3, ptrs[2], None) == 1
+    assert lib.qex_pack_links_pair(h, ptrs[0], ptrs[1], 0, ptrs[2], None) == 1
+    assert b"FP32" in lib.qex_last_error()
+    assert lib.qex_pack_links_pair(h, ptrs[0], ptrs[1], 7, ptrs[2], None) == 1
+    # true residual: NULL inputs, then a NULL result or an unknown arithmetic (refused before any launch)
+    rel = ctypes.c_double()
+    assert lib.qex_true_residual(h, None, None, 0.0, 0.1, ptrs[0], ptrs[1], 0, ctypes.byref(rel), None) == 1
+    assert lib.qex_true_residual(h, ptrs[2], None, 0.0, 0.1, ptrs[0], ptrs[1], 0, None, None) == 1
+    assert lib.qex_true_residual(h, ptrs[2], None, 0.0, 0.1, ptrs[0], ptrs[1], 2, ctypes.byref(rel), None) == 1
+    assert b"arith" in lib.qex_last_error()
     # long-link format per operator precision: two-row storage never applies to long links
     assert [lib.qex_long_links_prec(p) for p in range(6)] == [0, 1, 1, 4, 4, -1]
     lib.qex_lattice_destroy(h)
