@@ -125,8 +125,8 @@ def exported_symbols():
     """Names of the C entry points this binding wraps."""
     return ["qex_lattice_create", "qex_lattice_destroy", "qex_volume", "qex_half_volume", "qex_eo_index",
             "qex_neighbor_table", "qex_neighbor_table_device", "qex_links_bytes", "qex_field_bytes",
-            "qex_pack_links", "qex_pack_links_pair", "qex_unpack_links", "qex_pack_field", "qex_unpack_field", "qex_convert_links",
-            "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
+            "qex_pack_links", "qex_pack_links_pair", "qex_unpack_links", "qex_pack_field", "qex_unpack_field",
+            "qex_convert_links", "qex_convert_field", "qex_dslash", "qex_normal_op", "qex_norm2", "qex_dot", "qex_cg",
             "qex_cg_host", "qex_cg_profile", "qex_force", "qex_dslash_mrhs", "qex_cg_mrhs", "qex_cg_batch",
             "qex_cg_batch_tune_info", "qex_cg_batch_tune_set", "qex_long_links_prec", "qex_tune", "qex_tune_info",
             "qex_tune_set", "qex_fma_rates", "qex_true_residual", "qex_launch_count", "qex_last_error",

@@ -319,7 +319,8 @@ static qex_status build_graph(Solve &s, CgGraph **out) {
             ip.conditional.size = 1;
             e = cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip);
         }
-        if (!st && !e) e = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (!st && !e)
+            e = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
         cudaGraph_t captured = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
         if (st) break;

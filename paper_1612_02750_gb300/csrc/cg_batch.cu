@@ -667,7 +667,8 @@ static qex_status build_batch_graph(BatchCtx *c, const BatchLaunch &b) {
             ip.conditional.size = 1;
             e = cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip);
         }
-        if (!st && !e) e = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (!st && !e)
+            e = cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
         cudaGraph_t captured = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
         if (st) break;
@@ -985,7 +986,8 @@ extern "C" qex_status qex_cg_batch(int n, const qex_cg_item *items, qex_prec inn
             QEX_CUDA(cudaGraphLaunch(c->exec, s));
             if ((st = fetch())) return st;
             note_launches(3ull * (unsigned long long)(h->trips + h->idle_iters) +
-                          (mixed ? 6ull : 4ull) * (unsigned long long)(h->reliable_updates > 1 ? h->reliable_updates - 1 : 0));
+                          (mixed ? 6ull : 4ull) *
+                              (unsigned long long)(h->reliable_updates > 1 ? h->reliable_updates - 1 : 0));
         } else {
             const int batch = 8;
             while (!st && !h->error && !h->halt) {

@@ -426,9 +426,11 @@ qex_status qex_unpack_field(const qex_lattice *lat, qex_prec prec, int parity, c
     }
     int nb = blocks_for(lat->vh);
     if (is_f64(prec))
-        unpack_field_kernel<double><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const double *)half, lex_field);
+        unpack_field_kernel<double>
+            <<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const double *)half, lex_field);
     else
-        unpack_field_kernel<float><<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const float *)half, lex_field);
+        unpack_field_kernel<float>
+            <<<nb, kBlock, 0, as_stream(stream)>>>(lat->geom, parity, (const float *)half, lex_field);
     QEX_CHECK_LAUNCH("unpack_field_kernel");
     return QEX_OK;
 }
